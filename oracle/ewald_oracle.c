@@ -1,0 +1,424 @@
+/*
+ * Plain FP64 CPU oracle for periodic Ewald summation (TEST INFRASTRUCTURE).
+ *
+ * This file is the correctness reference for the GPU library.  Only the
+ * tests, the package smoke check and the benchmark's CPU-baseline leg may
+ * load it; the product path never calls it.  It shares no code, header,
+ * table or constant with the CUDA path.
+ *
+ * What it computes (Thorpe, Smith, Hasnip & Drummond, "Acceleration of the
+ * CASINO quantum Monte Carlo software using GPUs and OpenACC", Sec. 2.2:
+ * Eqs. (2)-(4) for 3D, Eqs. (5)-(6) for 2D with every charge at z = 0):
+ *
+ *   V = sum_{i<j} q_i q_j v_E(r_i - r_j) + 1/2 sum_j q_j^2 v_M
+ *
+ * written with alpha = sqrt(paper gamma) so that the screening function is
+ * erfc(alpha r).  Expanding v_E and v_M and collecting terms gives five
+ * pieces, each returned separately:
+ *
+ *   E_real  = sum_{i<j} q_i q_j sum_{R : |d_ij+R| < r_c} erfc(alpha|d_ij+R|)/|d_ij+R|
+ *   E_madR  = 1/2 sum_i q_i^2 sum_{R != 0, |R| < r_c} erfc(alpha|R|)/|R|
+ *   E_recip = C sum_{G != 0, |G| <= g_c} f(G) |rho(G)|^2,  rho(G) = sum_i q_i e^{iG.r_i}
+ *             3D: C = 2 pi / Omega,  f(G) = exp(-G^2/(4 alpha^2)) / G^2
+ *             2D: C = pi / A,        f(G) = erfc(G/(2 alpha)) / G
+ *   E_self  = -(alpha/sqrt(pi)) sum_i q_i^2
+ *   E_bg    = 3D: -pi Q^2 / (2 Omega alpha^2);   2D: -sqrt(pi) Q^2 / (A alpha)
+ *
+ * (Q = sum_i q_i.)  The reciprocal pieces of v_E and v_M combine into
+ * (C) sum_G f |rho|^2 because |rho|^2 = sum_j q_j^2 + 2 sum_{i<j} q_i q_j cos(G.r_ij);
+ * the constant -pi/(Omega gamma) of 3D v_E and v_M sums to the background
+ * term; -2 sqrt(gamma/pi) of v_M is the self term.  In 2D at z = 0 the two
+ * erfc terms of the reciprocal sum coincide and the bracket of v_E reduces
+ * to 1/(alpha sqrt(pi)).
+ *
+ * The single-particle move (Sec. 2.1: VMC and DMC sampling keep asking for the
+ * potential-energy change of a one-particle move) is computed by
+ * oracle_delta_e straight from its definition, with its own rho(G).
+ *
+ * Everything is a literal double loop: every lattice vector R whose integer
+ * coordinates could place d+R inside the cutoff sphere is visited, and every
+ * G vector (both +G and -G) inside the G sphere is summed with direct
+ * cos/sin per particle.  No blocking, no recurrences, no symmetry tricks.
+ *
+ * Parity status: pinned (bcc and hexagonal Wigner-crystal Madelung energies,
+ * rocksalt Madelung constant, alpha independence, invariances, supercell
+ * consistency, continuity of v_E - 1/r, brute-force rho identity, move dE
+ * against two full energies).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_LATTICE 2
+#define ORC_ERR_COINCIDENT 3
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef struct {
+    int dim;
+    double a[3][3]; /* a[i] = lattice vector i (rows), unused components 0 */
+    double b[3][3]; /* b[j] = reciprocal vector j, a_i . b_j = 2 pi delta_ij */
+    double vol;     /* |volume| (3D) or |area| (2D) */
+} cell_t;
+
+static double dot(int dim, const double *x, const double *y) {
+    double s = 0.0;
+    for (int k = 0; k < dim; ++k) s += x[k] * y[k];
+    return s;
+}
+
+static double norm(int dim, const double *x) { return sqrt(dot(dim, x, x)); }
+
+/* Reciprocal lattice from cross products (3D) or the 2D rotation. */
+static int make_cell(int dim, const double *lat, cell_t *c) {
+    if (dim != 2 && dim != 3) return ORC_ERR_ARG;
+    memset(c, 0, sizeof(*c));
+    c->dim = dim;
+    for (int i = 0; i < dim; ++i)
+        for (int k = 0; k < dim; ++k) c->a[i][k] = lat[i * dim + k];
+    if (dim == 3) {
+        double *a1 = c->a[0], *a2 = c->a[1], *a3 = c->a[2];
+        double c23[3] = {a2[1] * a3[2] - a2[2] * a3[1], a2[2] * a3[0] - a2[0] * a3[2],
+                         a2[0] * a3[1] - a2[1] * a3[0]};
+        double c31[3] = {a3[1] * a1[2] - a3[2] * a1[1], a3[2] * a1[0] - a3[0] * a1[2],
+                         a3[0] * a1[1] - a3[1] * a1[0]};
+        double c12[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2],
+                         a1[0] * a2[1] - a1[1] * a2[0]};
+        double v = a1[0] * c23[0] + a1[1] * c23[1] + a1[2] * c23[2];
+        if (!(fabs(v) > 0.0)) return ORC_ERR_LATTICE;
+        for (int k = 0; k < 3; ++k) {
+            c->b[0][k] = 2.0 * M_PI * c23[k] / v;
+            c->b[1][k] = 2.0 * M_PI * c31[k] / v;
+            c->b[2][k] = 2.0 * M_PI * c12[k] / v;
+        }
+        c->vol = fabs(v);
+    } else {
+        double *a1 = c->a[0], *a2 = c->a[1];
+        double s = a1[0] * a2[1] - a1[1] * a2[0];
+        if (!(fabs(s) > 0.0)) return ORC_ERR_LATTICE;
+        c->b[0][0] = 2.0 * M_PI * a2[1] / s;
+        c->b[0][1] = -2.0 * M_PI * a2[0] / s;
+        c->b[1][0] = -2.0 * M_PI * a1[1] / s;
+        c->b[1][1] = 2.0 * M_PI * a1[0] / s;
+        c->vol = fabs(s);
+    }
+    return ORC_OK;
+}
+
+/* Displacement d brought to fractional coordinates in [-1/2, 1/2]. */
+static void wrap(const cell_t *c, const double *d, double *dw) {
+    int dim = c->dim;
+    double f[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+        f[k] = dot(dim, c->b[k], d) / (2.0 * M_PI);
+        f[k] -= nearbyint(f[k]);
+    }
+    for (int x = 0; x < dim; ++x) {
+        dw[x] = 0.0;
+        for (int k = 0; k < dim; ++k) dw[x] += f[k] * c->a[k][x];
+    }
+}
+
+/*
+ * Sum over lattice vectors R of erfc(alpha|d+R|)/|d+R| for |d+R| < r_c.
+ * d is wrapped first; any R with |d+R| < r_c has |R| < r_c + |d| and hence
+ * integer coordinates |m_k| = |R.b_k|/2pi <= (r_c + |d|)|b_k|/2pi, so the box
+ * below contains every contributing R.  skip_origin drops R = 0 (used for the
+ * Madelung self-image sum).  Returns ORC_ERR_COINCIDENT if some |d+R| is
+ * below 1e-10 of the cell's length scale (two particles on top of each other
+ * up to the rounding of the wrap).
+ */
+static int image_sum(const cell_t *c, const double *d, double alpha, double r_c,
+                     int skip_origin, double *out) {
+    int dim = c->dim;
+    double dw[3] = {0, 0, 0};
+    wrap(c, d, dw);
+    double dn = norm(dim, dw);
+    int mmax[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k)
+        mmax[k] = (int)ceil((r_c + dn) * norm(dim, c->b[k]) / (2.0 * M_PI));
+    double s = 0.0;
+    int m[3];
+    for (m[0] = -mmax[0]; m[0] <= mmax[0]; ++m[0])
+        for (m[1] = -mmax[1]; m[1] <= mmax[1]; ++m[1])
+            for (m[2] = -mmax[2]; m[2] <= mmax[2]; ++m[2]) {
+                if (skip_origin && m[0] == 0 && m[1] == 0 && m[2] == 0) continue;
+                double x[3] = {0, 0, 0};
+                for (int y = 0; y < dim; ++y) {
+                    x[y] = dw[y];
+                    for (int k = 0; k < dim; ++k) x[y] += m[k] * c->a[k][y];
+                }
+                double r = norm(dim, x);
+                if (r < r_c) {
+                    if (r < 1e-10 * pow(c->vol, 1.0 / dim)) return ORC_ERR_COINCIDENT;
+                    s += erfc(alpha * r) / r;
+                }
+            }
+    *out = s;
+    return ORC_OK;
+}
+
+/* Reciprocal weight f(G) of the 3D and 2D sums. */
+static double recip_weight(int dim, double g, double alpha) {
+    if (dim == 3) return exp(-g * g / (4.0 * alpha * alpha)) / (g * g);
+    return erfc(g / (2.0 * alpha)) / g;
+}
+
+static double recip_prefactor(const cell_t *c) {
+    return c->dim == 3 ? 2.0 * M_PI / c->vol : M_PI / c->vol;
+}
+
+/*
+ * Visit every G = sum_k n_k b_k with 0 < |G| <= g_c.  Since n_k = G.a_k/2pi,
+ * |n_k| <= g_c |a_k| / 2pi bounds the box.  The callback gets G and |G|.
+ */
+typedef void (*gvisit_fn)(const double *G, double g, const int *n, void *ctx);
+
+static void for_each_g(const cell_t *c, double g_c, gvisit_fn fn, void *ctx) {
+    int dim = c->dim;
+    int nmax[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k)
+        nmax[k] = (int)ceil(g_c * norm(dim, c->a[k]) / (2.0 * M_PI));
+    int n[3];
+    for (n[0] = -nmax[0]; n[0] <= nmax[0]; ++n[0])
+        for (n[1] = -nmax[1]; n[1] <= nmax[1]; ++n[1])
+            for (n[2] = -nmax[2]; n[2] <= nmax[2]; ++n[2]) {
+                if (n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+                double G[3] = {0, 0, 0};
+                for (int y = 0; y < dim; ++y)
+                    for (int k = 0; k < dim; ++k) G[y] += n[k] * c->b[k][y];
+                double g = norm(dim, G);
+                if (g <= g_c) fn(G, g, n, ctx);
+            }
+}
+
+typedef struct {
+    int dim, n;
+    const double *pos, *q;
+    double alpha;
+    double sum;
+    long count;
+} recip_ctx;
+
+/* f(G) |rho(G)|^2 with rho summed directly with cos and sin. */
+static void visit_recip(const double *G, double g, const int *nvec, void *vctx) {
+    (void)nvec;
+    recip_ctx *r = (recip_ctx *)vctx;
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < r->n; ++i) {
+        double ph = dot(r->dim, G, r->pos + (size_t)i * r->dim);
+        re += r->q[i] * cos(ph);
+        im += r->q[i] * sin(ph);
+    }
+    r->sum += recip_weight(r->dim, g, r->alpha) * (re * re + im * im);
+    r->count += 1;
+}
+
+/* f(G) sum_{i,j} q_i q_j cos(G.(r_i - r_j)): the same sum without rho. */
+static void visit_recip_pairs(const double *G, double g, const int *nvec, void *vctx) {
+    (void)nvec;
+    recip_ctx *r = (recip_ctx *)vctx;
+    double s = 0.0;
+    for (int i = 0; i < r->n; ++i)
+        for (int j = 0; j < r->n; ++j) {
+            double d[3] = {0, 0, 0};
+            for (int y = 0; y < r->dim; ++y)
+                d[y] = r->pos[(size_t)i * r->dim + y] - r->pos[(size_t)j * r->dim + y];
+            s += r->q[i] * r->q[j] * cos(dot(r->dim, G, d));
+        }
+    r->sum += recip_weight(r->dim, g, r->alpha) * s;
+    r->count += 1;
+}
+
+static void visit_count(const double *G, double g, const int *nvec, void *vctx) {
+    (void)G; (void)g; (void)nvec;
+    ((recip_ctx *)vctx)->count += 1;
+}
+
+static int check_common(int dim, const double *lattice, int n, const double *pos,
+                        const double *q, double alpha, double r_c, double g_c) {
+    if ((dim != 2 && dim != 3) || !lattice || n < 1 || !pos || !q) return ORC_ERR_ARG;
+    if (!(alpha > 0.0) || !(r_c > 0.0) || !(g_c > 0.0)) return ORC_ERR_ARG;
+    return ORC_OK;
+}
+
+/*
+ * Full Ewald energy of one configuration.  comp (may be NULL) receives
+ * {E_real, E_madR, E_recip, E_self, E_bg}; *e receives their sum.
+ */
+int oracle_energy(int dim, const double *lattice, int n, const double *pos, const double *q,
+                  double alpha, double r_c, double g_c, double *comp, double *e) {
+    int st = check_common(dim, lattice, n, pos, q, alpha, r_c, g_c);
+    if (st) return st;
+    cell_t c;
+    if ((st = make_cell(dim, lattice, &c))) return st;
+
+    double e_real = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            double d[3] = {0, 0, 0}, s;
+            for (int y = 0; y < dim; ++y)
+                d[y] = pos[(size_t)i * dim + y] - pos[(size_t)j * dim + y];
+            if ((st = image_sum(&c, d, alpha, r_c, 0, &s))) return st;
+            e_real += q[i] * q[j] * s;
+        }
+
+    double zero[3] = {0, 0, 0}, smad, q2 = 0.0, qsum = 0.0;
+    if ((st = image_sum(&c, zero, alpha, r_c, 1, &smad))) return st;
+    for (int i = 0; i < n; ++i) {
+        q2 += q[i] * q[i];
+        qsum += q[i];
+    }
+    double e_madR = 0.5 * q2 * smad;
+
+    recip_ctx rc = {dim, n, pos, q, alpha, 0.0, 0};
+    for_each_g(&c, g_c, visit_recip, &rc);
+    double e_recip = recip_prefactor(&c) * rc.sum;
+
+    double e_self = -alpha / sqrt(M_PI) * q2;
+    double e_bg = dim == 3 ? -M_PI * qsum * qsum / (2.0 * c.vol * alpha * alpha)
+                           : -sqrt(M_PI) * qsum * qsum / (c.vol * alpha);
+    if (comp) {
+        comp[0] = e_real;
+        comp[1] = e_madR;
+        comp[2] = e_recip;
+        comp[3] = e_self;
+        comp[4] = e_bg;
+    }
+    *e = e_real + e_madR + e_recip + e_self + e_bg;
+    return ORC_OK;
+}
+
+/*
+ * Change of the Ewald energy when particle k moves to r_new, computed
+ * directly: the pair terms of k with every other particle at the new and old
+ * positions, and the reciprocal sum with rho and rho + delta, where
+ * delta(G) = q_k (e^{iG.r_new} - e^{iG.r_k}).  The Madelung, self and
+ * background pieces do not depend on positions and cancel.
+ */
+typedef struct {
+    int dim, n, k;
+    const double *pos, *q, *r_new;
+    double alpha;
+    double sum;
+} move_ctx;
+
+static void visit_move(const double *G, double g, const int *nvec, void *vctx) {
+    (void)nvec;
+    move_ctx *m = (move_ctx *)vctx;
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < m->n; ++i) {
+        double ph = dot(m->dim, G, m->pos + (size_t)i * m->dim);
+        re += m->q[i] * cos(ph);
+        im += m->q[i] * sin(ph);
+    }
+    double ph_new = dot(m->dim, G, m->r_new);
+    double ph_old = dot(m->dim, G, m->pos + (size_t)m->k * m->dim);
+    double dre = m->q[m->k] * (cos(ph_new) - cos(ph_old));
+    double dim_ = m->q[m->k] * (sin(ph_new) - sin(ph_old));
+    double after = (re + dre) * (re + dre) + (im + dim_) * (im + dim_);
+    double before = re * re + im * im;
+    m->sum += recip_weight(m->dim, g, m->alpha) * (after - before);
+}
+
+int oracle_delta_e(int dim, const double *lattice, int n, const double *pos, const double *q,
+                   int k, const double *r_new, double alpha, double r_c, double g_c,
+                   double *de) {
+    int st = check_common(dim, lattice, n, pos, q, alpha, r_c, g_c);
+    if (st) return st;
+    if (k < 0 || k >= n || !r_new || !de) return ORC_ERR_ARG;
+    cell_t c;
+    if ((st = make_cell(dim, lattice, &c))) return st;
+
+    double d_real = 0.0;
+    for (int j = 0; j < n; ++j) {
+        if (j == k) continue;
+        double dn[3] = {0, 0, 0}, dold[3] = {0, 0, 0}, sn, so;
+        for (int y = 0; y < dim; ++y) {
+            dn[y] = r_new[y] - pos[(size_t)j * dim + y];
+            dold[y] = pos[(size_t)k * dim + y] - pos[(size_t)j * dim + y];
+        }
+        if ((st = image_sum(&c, dn, alpha, r_c, 0, &sn))) return st;
+        if ((st = image_sum(&c, dold, alpha, r_c, 0, &so))) return st;
+        d_real += q[k] * q[j] * (sn - so);
+    }
+    move_ctx mc = {dim, n, k, pos, q, r_new, alpha, 0.0};
+    for_each_g(&c, g_c, visit_move, &mc);
+    *de = d_real + recip_prefactor(&c) * mc.sum;
+    return ORC_OK;
+}
+
+/* rho(G) = sum_i q_i e^{iG.r_i} at the integer G coordinates nvec[g][dim]. */
+int oracle_rho_at(int dim, const double *lattice, int n, const double *pos, const double *q,
+                  int n_g, const int *nvec, double *rho /* [n_g][2] */) {
+    if ((dim != 2 && dim != 3) || !lattice || n < 0 || n_g < 0 || !nvec || !rho)
+        return ORC_ERR_ARG;
+    cell_t c;
+    int st = make_cell(dim, lattice, &c);
+    if (st) return st;
+    for (int g = 0; g < n_g; ++g) {
+        double G[3] = {0, 0, 0};
+        for (int y = 0; y < dim; ++y)
+            for (int k = 0; k < dim; ++k) G[y] += nvec[(size_t)g * dim + k] * c.b[k][y];
+        double re = 0.0, im = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double ph = dot(dim, G, pos + (size_t)i * dim);
+            re += q[i] * cos(ph);
+            im += q[i] * sin(ph);
+        }
+        rho[2 * g] = re;
+        rho[2 * g + 1] = im;
+    }
+    return ORC_OK;
+}
+
+/* E_recip written as the double sum over particle pairs (no rho). */
+int oracle_recip_pairsum(int dim, const double *lattice, int n, const double *pos,
+                         const double *q, double alpha, double g_c, double *e_recip) {
+    if ((dim != 2 && dim != 3) || !lattice || n < 1 || !pos || !q || !(alpha > 0) ||
+        !(g_c > 0) || !e_recip)
+        return ORC_ERR_ARG;
+    cell_t c;
+    int st = make_cell(dim, lattice, &c);
+    if (st) return st;
+    recip_ctx rc = {dim, n, pos, q, alpha, 0.0, 0};
+    for_each_g(&c, g_c, visit_recip_pairs, &rc);
+    *e_recip = recip_prefactor(&c) * rc.sum;
+    return ORC_OK;
+}
+
+/* Number of G != 0 with |G| <= g_c (both members of each +-G pair). */
+long oracle_gcount(int dim, const double *lattice, double g_c) {
+    cell_t c;
+    if (make_cell(dim, lattice, &c)) return -1;
+    recip_ctx rc = {dim, 0, NULL, NULL, 1.0, 0.0, 0};
+    for_each_g(&c, g_c, visit_count, &rc);
+    return rc.count;
+}
+
+/*
+ * Cutoffs from a tolerance: erfc(alpha r_c) = tol for real space; for
+ * reciprocal space exp(-g_c^2/(4 alpha^2)) = tol in 3D and
+ * erfc(g_c/(2 alpha)) = tol in 2D.  erfc is inverted by bisection.
+ */
+static double erfc_inverse(double tol) {
+    double lo = 0.0, hi = 30.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (erfc(mid) > tol) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+int oracle_cutoffs(int dim, double alpha, double tol, double *r_c, double *g_c) {
+    if ((dim != 2 && dim != 3) || !(alpha > 0) || !(tol > 0 && tol < 1) || !r_c || !g_c)
+        return ORC_ERR_ARG;
+    double x = erfc_inverse(tol);
+    *r_c = x / alpha;
+    *g_c = dim == 3 ? 2.0 * alpha * sqrt(-log(tol)) : 2.0 * alpha * x;
+    return ORC_OK;
+}
