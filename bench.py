@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the Ewald hot path on GB300.
+
+One step = one full Ewald energy of every walker of the batch (structure
+factor + reciprocal energy, real-space pair sum, combine) followed by
+--moves rounds of single-electron propose + accept for every walker.  The
+headline value is walker Ewald energies per second of the mixed-precision
+batched form; move dE/s, the plain-FP64 form, the end-to-end numbers through
+host buffers, the roofline of the dominant kernel, the CPU oracle baseline
+and the SM clocks are reported on the same JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 it is launched with torch.distributed.run, one rank per GPU; each
+rank evaluates its own batch (walkers are independent: weak scaling, no
+data-path collective).  Timing: CUDA events on the library's stream, barrier
+and synchronize on both sides, max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker Ewald energies/s + move ΔE/s, mixed batched vs plain FP64; p50/p99 ms"
+FLOP_REAL_TERM = 25   # per real-space term inside r_c
+FLOP_G_TERM = 16      # per (electron, G) structure-factor term
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="heg3d_fcc_n1024")
+    p.add_argument("--walkers", type=int, default=0, help="0 = the workload's walker count")
+    p.add_argument("--moves", type=int, default=4, help="propose+accept rounds per step")
+    p.add_argument("--fp64-steps", type=int, default=2)
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of the GPU in use while the timed region runs."""
+    Q = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus = bus_id.lower() if bus_id else ""
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9 or (self.bus and not c[0].lower().endswith(self.bus)):
+                continue
+            try:
+                rows.append((float(c[1]), float(c[2]), c[5:9]))
+            except ValueError:
+                pass
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_walker_energies(w, walkers, rc, gc, threads):
+    """Oracle energies of the given walkers on `threads` host threads (ctypes releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    pos_all = np.concatenate([w["pos"][list(walkers)], np.broadcast_to(
+        w["fixed_pos"], (len(walkers),) + w["fixed_pos"].shape)], axis=1)
+    q = np.concatenate([w["q"], w["fixed_q"]])
+
+    def one(i):
+        return oracle.energy(w["dim"], w["lattice"], pos_all[i], q, w["alpha"], rc, gc)[0]
+
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(one, range(len(walkers))))
+
+
+def cpu_oracle_rate(w, rc, gc, seconds):
+    """Walker energies/s of the oracle on all host cores, on a bounded sample."""
+    import oracle
+    cores = host_cores()
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle_walker_energies(w, [0], rc, gc, 1)
+    t1 = time.perf_counter() - t0
+    per_round = t1  # one walker per core per round
+    rounds = max(1, min(4, int(seconds / max(per_round, 1e-3))))
+    n = cores * rounds
+    walkers = [i % w["n_walkers"] for i in range(n)]
+    t0 = time.perf_counter()
+    oracle_walker_energies(w, walkers, rc, gc, cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "walker energies/s", "cores": cores, "kind": "oracle",
+            "sample": "%d walkers of %s (%d per host thread), plain FP64 C oracle, %.1f s wall"
+                      % (n, w["name"], rounds, dt)}
+
+
+# ------------------------------------------------------------------- our arm
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+REAL_SOURCES = ["paper_2507_02888_gb300/csrc/energy_kernels.cu", "paper_2507_02888_gb300/csrc/device_common.cuh"]
+
+
+def profiled_traffic(workload, precision):
+    """DRAM bytes per launch of the real-space kernel from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", "real_%s_%s.json" % (precision, workload))
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != source_hash(REAL_SOURCES):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def expected_real_terms(info, w):
+    """Mean number of real-space terms per walker for uniform random displacements.
+
+    A uniformly distributed displacement has on average V_ball(r_c)/V_cell
+    lattice images inside the cutoff sphere.
+    """
+    dim, rc, vol = w["dim"], info["r_cutoff"], info["volume"]
+    ball = 4.0 / 3.0 * math.pi * rc ** 3 if dim == 3 else math.pi * rc ** 2
+    n, nf = w["n"], len(w["fixed_q"])
+    return (n * (n - 1) / 2 + n * nf) * ball / vol
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2507_02888_gb300 import ewald, inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = inputs.workload(args.workload, args.walkers or None)
+    W, N, dim = w["n_walkers"], w["n"], w["dim"]
+    stream = torch.cuda.Stream(device=dev)
+    pos_d = torch.tensor(w["pos"], device=dev)
+    rng = np.random.default_rng(1000 + rank)
+    M = args.moves
+    ks, disp, acc = inputs.move_stream(rng, W, N, max(M, 1), dim, w["sigma"])
+    k_d = torch.tensor(ks, device=dev)
+    rn_d = torch.tensor(w["pos"][np.arange(W)[None, :], ks] + disp, device=dev)
+    acc_d = torch.tensor(acc, device=dev)
+    e_d = torch.empty(W, dtype=torch.float64, device=dev)
+    de_d = torch.empty((max(M, 1), W), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def make(prec):
+        ctx = ewald.context_for(w, precision=prec, stream=stream)
+        b = ewald.Batch(ctx, W)
+        b.set_positions(pos_d)
+        return ctx, b
+
+    def timed_steps(b, ctx, steps, warmup, moves, clocks=None):
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for s in range(warmup):
+                b.energy(e_d)
+                for m in range(moves):
+                    b.propose(k_d[m], rn_d[m], de_d[m])
+                    b.accept(acc_d[m])
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            ctx.timing()          # drop warm-up timers
+            ctx.set_timing(True)
+            if clocks:
+                clocks.start()
+            for s in range(steps):
+                flush.fill_(float(s))            # evict the previous step's data from L2
+                ev[s][0].record(stream)
+                b.energy(e_d)
+                ev[s][1].record(stream)
+                for m in range(moves):
+                    b.propose(k_d[m], rn_d[m], de_d[m])
+                    b.accept(acc_d[m])
+                ev[s][2].record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop() if clocks else None
+            if world > 1:
+                torch.distributed.barrier()
+        ctx.set_timing(False)
+        t_e = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(steps))
+        t_m = sum(ev[s][1].elapsed_time(ev[s][2]) for s in range(steps))
+        return t_e, t_m, ctx.timing(), clk
+
+    def max_over_ranks(vals):
+        if world == 1:
+            return vals
+        t = torch.tensor(vals, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return t.tolist()
+
+    # ---- mixed precision, batched: the headline
+    ctx, b = make("mixed")
+    info = ctx.info()
+    props = torch.cuda.get_device_properties(dev)
+    bus = ("%02x:%02x.0" % (props.pci_bus_id, props.pci_device_id)
+           if isinstance(getattr(props, "pci_bus_id", None), int) else "")
+    clocks = ClockSampler(bus)
+    t_e, t_m, timers, clk = timed_steps(b, ctx, args.steps, args.warmup, M, clocks)
+    t_e, t_m = max_over_ranks([t_e, t_m])
+    K = args.steps
+    energies_per_s = world * W * K / (t_e / 1e3)
+    moves_per_s = world * W * M * K / (t_m / 1e3) if M else None
+    launches = sum(n for _, n in timers.values())
+
+    # dominant kernel: real-space pair sum
+    real_ms, real_n = timers["real"]
+    terms = expected_real_terms(info, w) * W
+    achieved = terms * FLOP_REAL_TERM / (real_ms / real_n / 1e3) / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = profiled_traffic(args.workload, "mixed")
+    sf_ms, sf_n = timers["sfac"]
+    kernel_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in timers.items() if v[1]}
+
+    result = {
+        "metric": METRIC, "value": energies_per_s, "unit": "walker energies/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": (t_e + t_m) / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "walkers_per_gpu": W, "n_electrons": N,
+                   "n_fixed": len(w["fixed_q"]), "dim": dim, "alpha": info["alpha"],
+                   "r_cutoff": info["r_cutoff"], "n_g_half": info["n_g_half"],
+                   "moves_per_step": M, "precision": "mixed",
+                   "l2": "flushed before every timed step (256 MB write); positions+rho %.0f MB > L2"
+                         % (W * (N * dim * 8 + info["n_runs"] * info["run_len"] * 16) / 1e6),
+                   "parallelism": "walker replicas, %d GPU(s)" % world},
+        "moves": {"value": moves_per_s, "unit": "move dE/s (propose+accept)",
+                  "ms_per_round": t_m / max(K * M, 1)},
+        "kernel_ms_per_launch": kernel_ms,
+        "roofline": {"bound": "alu", "kernel": "k_real<float,%d>" % dim, "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal)",
+                     "work": "%d flop per real-space term inside r_c, %.4g terms per launch"
+                             % (FLOP_REAL_TERM, terms),
+                     "sfac_tflops": FLOP_G_TERM * N * info["n_g_half"] * W / (sf_ms / sf_n / 1e3) / 1e12},
+        "clocks": clk, "gpu_launches": launches,
+    }
+    b.close()
+    ctx.close()
+
+    # ---- plain FP64 form, same workload
+    if not args.no_fp64:
+        ctx, b = make("fp64")
+        fs = max(1, args.fp64_steps)
+        f_e, f_m, f_t, _ = timed_steps(b, ctx, fs, 1, M)
+        f_e, f_m = max_over_ranks([f_e, f_m])
+        result["fp64"] = {"value": world * W * fs / (f_e / 1e3), "unit": "walker energies/s",
+                          "moves": world * W * M * fs / (f_m / 1e3) if M else None,
+                          "steps": fs, "kernel_ms_per_launch":
+                              {k: round(v[0] / max(v[1], 1), 3) for k, v in f_t.items() if v[1]}}
+        result["mixed_over_fp64"] = energies_per_s / result["fp64"]["value"]
+        b.close()
+        ctx.close()
+
+    # ---- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        ctx = ewald.context_for(w, precision="mixed", stream=stream)
+        b = ewald.Batch(ctx, W)
+        pos_h = np.ascontiguousarray(w["pos"])
+        ks_h, rn_h, acc_h = ks, np.ascontiguousarray(rn_d.cpu().numpy()), acc
+        e_steps = max(2, K // 2)
+        for _ in range(2):
+            b.set_positions(pos_h)
+            b.energy()
+        if world > 1:
+            torch.distributed.barrier()
+        te = tm = 0.0
+        for s in range(e_steps):
+            t0 = time.perf_counter()
+            b.set_positions(pos_h)
+            b.energy()
+            t1 = time.perf_counter()
+            for m in range(M):
+                b.propose(ks_h[m], rn_h[m])
+                b.accept(acc_h[m])
+            te += t1 - t0
+            tm += time.perf_counter() - t1
+        te, tm = max_over_ranks([te, tm])
+        result["e2e"] = {"value": world * W * e_steps / te, "unit": "walker energies/s",
+                         "h2d_bytes_per_step": W * N * dim * 8 + M * W * (4 + dim * 8 + 1),
+                         "d2h_bytes_per_step": W * 8 + M * W * 8,
+                         "moves": world * W * M * e_steps / tm if M else None,
+                         "note": "host positions uploaded, energies and dE read back every step"}
+        b.close()
+        ctx.close()
+
+    # ---- CPU oracle on the host cores (rank 0 only)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        result["cpu_baseline"] = cpu_oracle_rate(w, info["r_cutoff"], info["g_cutoff"], args.cpu_seconds)
+    return result
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: walker energies/s on the host cores."""
+    from paper_2507_02888_gb300 import inputs
+    import oracle
+    if rank != 0:
+        return None
+    w = inputs.workload(args.workload, args.walkers or None)
+    rc, gc = oracle.cutoffs(w["dim"], w["alpha"])
+    oracle.build()
+    cores = host_cores()
+    per_step = cores
+    for s in range(args.warmup):
+        oracle_walker_energies(w, [s % w["n_walkers"]], rc, gc, 1)
+    t = 0.0
+    for s in range(args.steps):
+        walkers = [(s * per_step + i) % w["n_walkers"] for i in range(per_step)]
+        t0 = time.perf_counter()
+        oracle_walker_energies(w, walkers, rc, gc, cores)
+        t += time.perf_counter() - t0
+    value = per_step * args.steps / t
+    return {"metric": METRIC, "value": value, "unit": "walker energies/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "walkers_per_step": per_step, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": "walker energies/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d walkers per step of %s on %d host threads" % (per_step, w["name"], cores)},
+            "e2e": {"value": value, "unit": "walker energies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")   # host-side barrier and timing max only
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

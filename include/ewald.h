@@ -1,0 +1,161 @@
+/*
+ * ewald.h - C ABI of the GB300 Ewald-summation library (libewald_gb300.so).
+ *
+ * The library evaluates the periodic Coulomb (Ewald) energy of a batch of
+ * quantum Monte Carlo walkers and the energy change of single-particle moves
+ * (Thorpe, Smith, Hasnip & Drummond, "Acceleration of the CASINO quantum
+ * Monte Carlo software using GPUs and OpenACC": Sec. 2.2, Eqs. (2)-(4) in 3D
+ * and Eqs. (5)-(6) in 2D with every charge in the plane z = 0; Sec. 2.1 for
+ * the single-particle moves of VMC/DMC).
+ *
+ * Conventions
+ *   - alpha ("gamma" below) is the screening parameter of erfc(alpha r); it
+ *     is the square root of the paper's gamma.
+ *   - Lattices are dim x dim, row-major, row i = lattice vector a_i (bohr).
+ *     The cell must be right-handed (det > 0).
+ *   - Positions are Cartesian, row-major [W][N][dim] (walker, particle, axis).
+ *   - Energies are in hartree (Coulomb constant 1).
+ *   - Every call that takes "on_device" reads or writes the caller's array
+ *     in device memory when on_device != 0, and in host memory otherwise.
+ *     Device arrays are accessed on the context's stream, in stream order.
+ *     Host outputs are complete when the call returns (the call synchronises
+ *     the stream); host inputs may be reused as soon as the call returns.
+ *   - The caller owns every array it passes; the library copies what it
+ *     needs and keeps no caller pointer.  The library owns all state it
+ *     allocates (walker positions, rho(G), tables) and frees it in the
+ *     matching destroy call.
+ *   - Every int-returning call returns EWALD_OK (0) or an error code.  The
+ *     last error is also kept per context (ewald_last_error).  Errors found
+ *     inside kernels (coincident particles, a move index out of range) are
+ *     reported by the next call that synchronises the stream, or by
+ *     ewald_batch_sync.
+ */
+#ifndef EWALD_GB300_H
+#define EWALD_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ewald_ctx ewald_ctx;     /* one periodic system: cell, charges, tables */
+typedef struct ewald_batch ewald_batch; /* W walkers of one system, state on the device */
+
+/* Arithmetic of the kernels (paper Sec. 6: single vs double precision).
+ * EWALD_FP64: every kernel in FP64.
+ * EWALD_MIXED: erfc, sin/cos and per-tile sums in FP32 with compensated
+ * accumulation; per-walker reductions, rho(G) and constants in FP64. */
+typedef enum { EWALD_FP64 = 0, EWALD_MIXED = 1 } ewald_precision;
+
+enum {
+    EWALD_OK = 0,
+    EWALD_ERR_ARG = 1,         /* bad dimension, NULL, size < 1, non-finite value, k out of range */
+    EWALD_ERR_LATTICE = 2,     /* singular or left-handed lattice */
+    EWALD_ERR_COINCIDENT = 3,  /* two particles (or images) closer than 1e-10 of the cell size */
+    EWALD_ERR_NO_PROPOSAL = 4, /* accept without a pending propose */
+    EWALD_ERR_OOM = 5,         /* device or host allocation failed, or over the memory budget */
+    EWALD_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+    EWALD_ERR_TIMEOUT = 7,     /* a bounded device-side wait expired */
+    EWALD_ERR_STATE = 8        /* call not valid in the object's current state */
+};
+
+typedef struct {
+    int dim;                     /* 2 or 3 */
+    const double *lattice;       /* [dim][dim] host memory, rows = lattice vectors */
+    int n_mobile;                /* number of moving particles (electrons), >= 1 */
+    const double *mobile_charge; /* [n_mobile] host memory */
+    int n_fixed;                 /* number of fixed particles (ions), >= 0 */
+    const double *fixed_pos;     /* [n_fixed][dim] host memory, Cartesian (may be NULL if 0) */
+    const double *fixed_charge;  /* [n_fixed] host memory (may be NULL if 0) */
+    double gamma;                /* alpha of erfc(alpha r); <= 0 picks a balanced alpha */
+    double g_cutoff;             /* |G| cutoff; <= 0: exp(-G^2/4alpha^2) (3D) or
+                                    erfc(G/2alpha) (2D) reaches 1e-16 */
+    double r_cutoff;             /* real-space cutoff; <= 0: erfc(alpha r) reaches 1e-16 */
+    int precision;               /* ewald_precision */
+    int resum_every;             /* accepted moves between rho(G) rebuilds; 0 -> 64 */
+} ewald_desc;
+
+/* Read-only facts about a context (for tests, manifests and tuning). */
+typedef struct {
+    int dim, n_mobile, n_fixed, precision;
+    double alpha, r_cutoff, g_cutoff;
+    double volume;        /* Omega (3D) or area A (2D) */
+    int n_g_half;         /* G vectors kept, one of each +-G pair */
+    int n_images;         /* distinct lattice vectors that may meet the real-space cutoff */
+    int subcell_bits;     /* real-space displacement cells: 2^bits per axis */
+    int max_candidates;   /* longest candidate-image list of a displacement cell */
+    int n_runs, run_len;  /* G rows split into runs of <= run_len consecutive n1 */
+    double e_madelung;    /* 1/2 sum q^2 sum_{R!=0} erfc(alpha R)/R  (all charges) */
+    double e_self;        /* -(alpha/sqrt(pi)) sum q^2                (all charges) */
+    double e_background;  /* -pi Q^2/(2 Omega alpha^2) (3D), -sqrt(pi) Q^2/(A alpha) (2D) */
+    double e_fixed_real;  /* real-space pair sum among fixed particles */
+} ewald_info;
+
+/* Create a context: validates the description, builds the G list, the image
+ * lists and the constants in FP64 on the host (paper Sec. 6.1 keeps these
+ * set-up tables in double precision) and uploads them once (Sec. 2.2: the
+ * Ewald data move to the GPU at the outset).  cuda_stream is a cudaStream_t;
+ * NULL makes the library create a blocking stream of its own.  On error
+ * *out is set to NULL. */
+int ewald_create(const ewald_desc *desc, void *cuda_stream, ewald_ctx **out);
+void ewald_destroy(ewald_ctx *ctx);
+int ewald_get_info(const ewald_ctx *ctx, ewald_info *info);
+/* The half-space G list in the library's storage order: nvec[n_g_half][dim]
+ * integer coordinates on the reciprocal basis (host memory). */
+int ewald_get_gvectors(const ewald_ctx *ctx, int *nvec);
+/* Last error recorded on the context (sticky until the next successful call
+ * that checks it). */
+int ewald_last_error(const ewald_ctx *ctx);
+const char *ewald_strerror(int code);
+
+/* Walker batches.  A batch owns the walkers' positions (fixed-point
+ * fractional coordinates), their rho(G) and the pending moves.  Before the
+ * first energy or move the positions must be set. */
+int ewald_batch_create(ewald_ctx *ctx, int n_walkers, ewald_batch **out);
+void ewald_batch_destroy(ewald_batch *b);
+/* pos: [W][N][dim] Cartesian.  Positions are stored wrapped into the cell;
+ * get_positions returns the wrapped positions. */
+int ewald_batch_set_positions(ewald_batch *b, const double *pos, int on_device);
+int ewald_batch_get_positions(ewald_batch *b, double *pos, int on_device);
+/* Synchronise the context's stream and report errors raised by kernels. */
+int ewald_batch_sync(ewald_batch *b);
+
+/* Full Ewald energy of every walker, e_out[W] (paper Eq. (2) with Eqs. (3)-(4)
+ * or (5)-(6)).  Also rebuilds each walker's rho(G) from scratch. */
+int ewald_energy(ewald_batch *b, double *e_out, int on_device);
+/* Same, with components comp_out[W][5] =
+ * {E_real, E_madelung, E_recip, E_self, E_background}; E_real includes the
+ * fixed-fixed pairs, and the other four include every charge.  Sum = energy. */
+int ewald_energy_components(ewald_batch *b, double *comp_out, int on_device);
+
+/* Propose moving particle k[w] of every walker w to r_new[w][dim]
+ * (Cartesian) and return the Ewald energy change de_out[W].  The move is
+ * remembered as pending; a second propose replaces it.  Cost O(N + N_G)
+ * per walker.  k, r_new and de_out are all host or all device arrays. */
+int ewald_propose_move(ewald_batch *b, const int *k, const double *r_new, double *de_out,
+                       int on_device);
+/* Apply the pending moves of the walkers with accept[w] != 0: position and
+ * rho(G) += delta(G) in FP64.  Every resum_every accepted moves of a walker
+ * its rho(G) is rebuilt from scratch.  EWALD_ERR_NO_PROPOSAL if nothing is
+ * pending. */
+int ewald_accept_move(ewald_batch *b, const unsigned char *accept, int on_device);
+/* Rebuild rho(G) of every walker from its positions. */
+int ewald_resum(ewald_batch *b);
+/* rho(G) of every walker, rho_out[W][n_g_half][2] (re, im), G in the order
+ * of ewald_get_gvectors; includes the fixed particles' contribution. */
+int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device);
+
+/* Kernel timers of a context (in the spirit of the paper's per-subroutine
+ * timers, Sec. 3.2).  When enabled, every kernel the context launches is
+ * bracketed by CUDA events on its stream.  ewald_get_timing synchronises
+ * the stream, writes the accumulated device milliseconds and launch counts
+ * of the EWALD_N_KERNELS kernels (ms[EWALD_N_KERNELS], launches[...], host
+ * memory; either may be NULL), and resets them.  Kernel order: ingest,
+ * structure factor, real space, combine, propose, accept, resum. */
+#define EWALD_N_KERNELS 7
+int ewald_set_timing(ewald_ctx *ctx, int enable);
+int ewald_get_timing(ewald_ctx *ctx, double *ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,617 @@
+// C ABI of the library (include/ewald.h): object lifetimes, argument checks,
+// host<->device staging and error reporting.  All numerical work is in the
+// kernels of energy_kernels.cu and move_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+
+using namespace ewald;
+
+struct ewald_ctx {
+    HostTables t;
+    SysDev s{};
+    LaunchCfg cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void *> dev;
+    int *d_g2slot = nullptr;
+    int n_batches = 0;        // live batches; the context outlives them
+    bool destroy_pending = false;
+    int last_error = EWALD_OK;
+    std::string why;
+    // kernel timers
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
+    double t_ms[KT_COUNT] = {};
+    long long t_n[KT_COUNT] = {};
+};
+
+struct ewald_batch {
+    ewald_ctx *ctx = nullptr;
+    BatchDev b{};
+    std::vector<void *> dev;
+    bool has_pos = false, has_pending = false;
+    bool counted = false;  // included in ctx->n_batches
+    // host-I/O staging: pinned host buffer and device scratch for host inputs
+    void *pin = nullptr;
+    size_t pin_bytes = 0;
+    double *d_io = nullptr;   // [W][N][dim] doubles (positions, rho, components)
+    size_t d_io_bytes = 0;
+    int *d_k = nullptr;
+    double *d_rnew = nullptr, *d_de = nullptr;
+    unsigned char *d_acc = nullptr;
+};
+
+namespace {
+
+int fail(ewald_ctx *c, int code, const char *why = nullptr) {
+    if (c && code) {
+        c->last_error = code;
+        if (why) c->why = why;
+    }
+    return code;
+}
+
+int cuda_fail(ewald_ctx *c, cudaError_t e) {
+    if (c) c->why = cudaGetErrorString(e);
+    return fail(c, EWALD_ERR_CUDA);
+}
+
+template <typename T>
+cudaError_t dalloc(std::vector<void *> &owned, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e == cudaSuccess) owned.push_back(*p);
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(std::vector<void *> &owned, T **p, const T *src, size_t count) {
+    cudaError_t e = dalloc(owned, p, count);
+    if (e) return e;
+    if (count) e = cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+unsigned long long to_fixed(double f) {
+    f -= std::floor(f);
+    if (f >= 1.0) f = 0.0;
+    return (unsigned long long)std::ldexp(f, 64);
+}
+
+int build_device(ewald_ctx *c) {
+    HostTables &t = c->t;
+    SysDev &s = c->s;
+    std::vector<void *> &o = c->dev;
+    const int dim = t.dim;
+    s.dim = dim;
+    s.n_mob = t.n_mob;
+    s.n_fix = t.n_fix;
+    s.mob_stride = (t.n_mob + 31) / 32 * 32;
+    s.fix_stride = std::max(1, (t.n_fix + 31) / 32 * 32);
+    for (int k = 0; k < 3; ++k)
+        for (int x = 0; x < 3; ++x) {
+            s.A[k][x] = t.A[k][x];
+            s.A64[k][x] = std::ldexp(t.A[k][x], -64);
+            s.A32[k][x] = (float)std::ldexp(t.A[k][x], -32);
+            s.Binv[k][x] = t.Ainv[x][k];
+        }
+    s.alpha = t.alpha;
+    s.alpha_f = (float)t.alpha;
+    s.alpha_lo_f = (float)(t.alpha - (double)s.alpha_f);
+    s.alpha2_f = (float)(t.alpha * t.alpha);
+    s.alpha2_lo_f = (float)(t.alpha * t.alpha - (double)s.alpha2_f);
+    s.rc2 = t.r_c * t.r_c;
+    s.rc2_f = (float)s.rc2;
+    double L = std::pow(t.volume, 1.0 / dim);
+    s.coin2 = 1e-20 * L * L;
+    s.coin2_f = (float)s.coin2;
+    cudaError_t e;
+    // images
+    int n_img = (int)t.img.size() / 3;
+    std::vector<Img64> imd(n_img);
+    std::vector<float4> imf(n_img);
+    for (int i = 0; i < n_img; ++i) {
+        imd[i] = Img64{t.img[3 * i], t.img[3 * i + 1], t.img[3 * i + 2], 0.0};
+        imf[i] = make_float4((float)t.img[3 * i], (float)t.img[3 * i + 1], (float)t.img[3 * i + 2], 0.f);
+    }
+    s.n_img = n_img;
+    s.sub_bits = t.sub_bits;
+    s.cand_max = t.cand_max;
+    if ((e = upload(o, (Img64 **)&s.img_d, imd.data(), imd.size()))) return cuda_fail(c, e);
+    if ((e = upload(o, (float4 **)&s.img_f, imf.data(), imf.size()))) return cuda_fail(c, e);
+    if ((e = upload(o, (unsigned short **)&s.cand, t.cand.data(), t.cand.size()))) return cuda_fail(c, e);
+    if ((e = upload(o, (int **)&s.cand_len, t.cand_len.data(), t.cand_len.size()))) return cuda_fail(c, e);
+    // pair tiles: 32 x S particles per side
+    int S = t.n_mob >= 128 ? 4 : (t.n_mob >= 64 ? 2 : 1);
+    if (const char *env = std::getenv("EWALD_TILE_SUBTILES")) {
+        int v = std::atoi(env);
+        if (v == 1 || v == 2 || v == 4) S = v;
+    }
+    s.tile = 32 * S;
+    s.n_mob_tiles = (t.n_mob + s.tile - 1) / s.tile;
+    int nft = (t.n_fix + s.tile - 1) / s.tile;
+    std::vector<int2> items;
+    for (int i = 0; i < s.n_mob_tiles; ++i) {
+        for (int j = i; j < s.n_mob_tiles; ++j) items.push_back(make_int2(i, j));
+        for (int f = 0; f < nft; ++f) items.push_back(make_int2(i, s.n_mob_tiles + f));
+    }
+    s.n_items = (int)items.size();
+    if ((e = upload(o, (int2 **)&s.items, items.data(), items.size()))) return cuda_fail(c, e);
+    // reciprocal
+    s.n_runs = (int)t.runs.size() / 4;
+    s.run_len = t.run_len;
+    s.n_gh = (int)t.g2slot.size();
+    s.n_gchunks = (s.n_runs + kSfacThreads - 1) / kSfacThreads;
+    s.n1max = std::max(t.n1max, 1);
+    s.n2max = std::max(t.n2max, 1);
+    s.n3max = std::max(t.n3max, 1);
+    std::vector<int4> runs(s.n_runs);
+    for (int r = 0; r < s.n_runs; ++r)
+        runs[r] = make_int4(t.runs[4 * r], t.runs[4 * r + 1], t.runs[4 * r + 2], t.runs[4 * r + 3]);
+    if ((e = upload(o, (int4 **)&s.runs, runs.data(), runs.size()))) return cuda_fail(c, e);
+    std::vector<float> gwf(t.gw.begin(), t.gw.end());
+    if ((e = upload(o, (double **)&s.gw_d, t.gw.data(), t.gw.size()))) return cuda_fail(c, e);
+    if ((e = upload(o, (float **)&s.gw_f, gwf.data(), gwf.size()))) return cuda_fail(c, e);
+    s.rho_fix = nullptr;
+    if (t.n_fix > 0) {
+        std::vector<double2> rf(t.rho_fix.size() / 2);
+        for (size_t i = 0; i < rf.size(); ++i) rf[i] = make_double2(t.rho_fix[2 * i], t.rho_fix[2 * i + 1]);
+        if ((e = upload(o, (double2 **)&s.rho_fix, rf.data(), rf.size()))) return cuda_fail(c, e);
+    }
+    if ((e = upload(o, &c->d_g2slot, t.g2slot.data(), t.g2slot.size()))) return cuda_fail(c, e);
+    // charges and fixed particles
+    std::vector<float> qmf(t.q_mob.begin(), t.q_mob.end()), qff(t.q_fix.begin(), t.q_fix.end());
+    if ((e = upload(o, (double **)&s.q_mob, t.q_mob.data(), t.q_mob.size()))) return cuda_fail(c, e);
+    if ((e = upload(o, (float **)&s.q_mob_f, qmf.data(), qmf.size()))) return cuda_fail(c, e);
+    if ((e = upload(o, (double **)&s.q_fix, t.q_fix.data(), t.q_fix.size()))) return cuda_fail(c, e);
+    if ((e = upload(o, (float **)&s.q_fix_f, qff.data(), qff.size()))) return cuda_fail(c, e);
+    std::vector<unsigned long long> fu((size_t)dim * s.fix_stride, 0ull);
+    for (int I = 0; I < t.n_fix; ++I)
+        for (int k = 0; k < dim; ++k) {
+            double f = 0;
+            for (int x = 0; x < dim; ++x) f += t.Ainv[x][k] * t.fix_pos[(size_t)I * dim + x];
+            fu[(size_t)k * s.fix_stride + I] = to_fixed(f);
+        }
+    if ((e = upload(o, (unsigned long long **)&s.fix_u, fu.data(), fu.size()))) return cuda_fail(c, e);
+    s.e_madR = t.e_madR;
+    s.e_self = t.e_self;
+    s.e_bg = t.e_bg;
+    s.e_II = t.e_II;
+    if ((e = (cudaError_t)configure_launch(s, t.precision, &c->cfg))) return cuda_fail(c, e);
+    return EWALD_OK;
+}
+
+cudaEvent_t take_event(ewald_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Run one launcher, bracketed by events when the context's timers are on.
+template <typename F>
+int timed(ewald_ctx *c, int kid, F &&launch) {
+    if (!c->timing) return launch();
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    cudaEventRecord(a, c->stream);
+    int e = launch();
+    cudaEventRecord(b, c->stream);
+    c->ev_open.push_back({kid, {a, b}});
+    return e;
+}
+
+int collect_timers(ewald_ctx *c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    for (auto &o : c->ev_open) {
+        float ms = 0;
+        if (!e) e = cudaEventElapsedTime(&ms, o.second.first, o.second.second);
+        c->t_ms[o.first] += ms;
+        c->t_n[o.first] += 1;
+        c->ev_pool.push_back(o.second.first);
+        c->ev_pool.push_back(o.second.second);
+    }
+    c->ev_open.clear();
+    return e;
+}
+
+void free_all(std::vector<void *> &v) {
+    for (void *p : v) cudaFree(p);
+    v.clear();
+}
+
+// Wait for the stream and turn device-side error bits into an error code.
+int sync_status(ewald_batch *b) {
+    ewald_ctx *c = b->ctx;
+    int *h = (int *)b->pin;
+    cudaError_t e = cudaMemcpyAsync(h, b->b.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e);
+    int st = *h;
+    if (!st) return EWALD_OK;
+    if ((e = cudaMemsetAsync(b->b.status, 0, sizeof(int), c->stream))) return cuda_fail(c, e);
+    if (st & ST_COINCIDENT) return fail(c, EWALD_ERR_COINCIDENT, "coincident particles");
+    if (st & ST_TIMEOUT) return fail(c, EWALD_ERR_TIMEOUT, "device wait timed out");
+    return fail(c, EWALD_ERR_ARG, st & ST_BAD_INDEX ? "move index or position invalid" : "non-finite position");
+}
+
+// Copy n bytes of device memory to a host or device destination.
+int copy_out(ewald_batch *b, void *dst, const void *src, size_t n, int on_device) {
+    ewald_ctx *c = b->ctx;
+    cudaError_t e;
+    if (on_device) {
+        e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, c->stream);
+        return e ? cuda_fail(c, e) : EWALD_OK;
+    }
+    // status word first, then the payload behind it in the pinned buffer
+    char *pin = (char *)b->pin;
+    e = cudaMemcpyAsync(pin + 16, src, n, cudaMemcpyDeviceToHost, c->stream);
+    if (e) return cuda_fail(c, e);
+    int st = sync_status(b);
+    std::memcpy(dst, pin + 16, n);
+    return st;
+}
+
+// Stage a host array into device scratch; returns the device pointer.
+const void *copy_in(ewald_batch *b, const void *src, size_t n, void *dscratch, int *err) {
+    ewald_ctx *c = b->ctx;
+    char *pin = (char *)b->pin + 16;
+    std::memcpy(pin, src, n);
+    cudaError_t e = cudaMemcpyAsync(dscratch, pin, n, cudaMemcpyHostToDevice, c->stream);
+    if (e) {
+        *err = cuda_fail(c, e);
+        return nullptr;
+    }
+    // the pinned buffer is reused by the next call: wait for the copy
+    if ((e = cudaStreamSynchronize(c->stream))) {
+        *err = cuda_fail(c, e);
+        return nullptr;
+    }
+    *err = EWALD_OK;
+    return dscratch;
+}
+
+// Structure factor + reciprocal energy, real-space pairs, combine (paper
+// Sec. 5.1: independent reciprocal and real-space loops, then a combine).
+int run_energy(ewald_batch *b) {
+    ewald_ctx *c = b->ctx;
+    const int p = c->t.precision;
+    int e = timed(c, KT_SFAC, [&] { return launch_sfac(c->s, b->b, p, c->cfg, nullptr, c->stream); });
+    if (!e) e = timed(c, KT_REAL, [&] { return launch_real(c->s, b->b, p, c->cfg, c->stream); });
+    if (!e) e = timed(c, KT_COMBINE, [&] { return launch_combine(c->s, b->b, c->stream); });
+    return e ? cuda_fail(c, (cudaError_t)e) : EWALD_OK;
+}
+
+bool ready(ewald_batch *b) {
+    if (!b || !b->ctx) return false;
+    if (!b->has_pos) {
+        fail(b->ctx, EWALD_ERR_STATE, "positions not set");
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ewald_strerror(int code) {
+    switch (code) {
+        case EWALD_OK: return "ok";
+        case EWALD_ERR_ARG: return "invalid argument";
+        case EWALD_ERR_LATTICE: return "singular or left-handed lattice";
+        case EWALD_ERR_COINCIDENT: return "coincident particles";
+        case EWALD_ERR_NO_PROPOSAL: return "accept without a pending proposal";
+        case EWALD_ERR_OOM: return "out of memory";
+        case EWALD_ERR_CUDA: return "CUDA runtime error";
+        case EWALD_ERR_TIMEOUT: return "device wait timed out";
+        case EWALD_ERR_STATE: return "call not valid in the current state";
+        default: return "unknown error";
+    }
+}
+
+int ewald_create(const ewald_desc *desc, void *cuda_stream, ewald_ctx **out) {
+    if (!out) return EWALD_ERR_ARG;
+    *out = nullptr;
+    ewald_ctx *c = new (std::nothrow) ewald_ctx();
+    if (!c) return EWALD_ERR_OOM;
+    int st = build_tables(desc, &c->t, &c->why);
+    if (st) {
+        delete c;
+        return st;
+    }
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreate(&c->stream);
+        if (e) {
+            delete c;
+            return EWALD_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    st = build_device(c);
+    if (st) {
+        ewald_destroy(c);
+        return st;
+    }
+    *out = c;
+    return EWALD_OK;
+}
+
+static void destroy_now(ewald_ctx *c) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    collect_timers(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    free_all(c->dev);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+void ewald_destroy(ewald_ctx *c) {
+    if (!c) return;
+    if (c->n_batches > 0) {  // freed when its last batch is destroyed
+        c->destroy_pending = true;
+        return;
+    }
+    destroy_now(c);
+}
+
+int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
+    if (!c || !i) return EWALD_ERR_ARG;
+    const HostTables &t = c->t;
+    i->dim = t.dim;
+    i->n_mobile = t.n_mob;
+    i->n_fixed = t.n_fix;
+    i->precision = t.precision;
+    i->alpha = t.alpha;
+    i->r_cutoff = t.r_c;
+    i->g_cutoff = t.g_c;
+    i->volume = t.volume;
+    i->n_g_half = (int)t.g2slot.size();
+    i->n_images = (int)t.img.size() / 3;
+    i->subcell_bits = t.sub_bits;
+    i->max_candidates = t.cand_max;
+    i->n_runs = (int)t.runs.size() / 4;
+    i->run_len = t.run_len;
+    i->e_madelung = t.e_madR;
+    i->e_self = t.e_self;
+    i->e_background = t.e_bg;
+    i->e_fixed_real = t.e_II;
+    return EWALD_OK;
+}
+
+int ewald_get_gvectors(const ewald_ctx *c, int *nvec) {
+    if (!c || !nvec) return EWALD_ERR_ARG;
+    std::memcpy(nvec, c->t.gn.data(), c->t.gn.size() * sizeof(int));
+    return EWALD_OK;
+}
+
+int ewald_last_error(const ewald_ctx *c) {
+    if (!c) return EWALD_ERR_ARG;
+    int e = c->last_error;
+    const_cast<ewald_ctx *>(c)->last_error = EWALD_OK;
+    return e;
+}
+
+int ewald_batch_create(ewald_ctx *c, int W, ewald_batch **out) {
+    if (!out) return fail(c, EWALD_ERR_ARG);
+    *out = nullptr;
+    if (!c || W < 1) return fail(c, EWALD_ERR_ARG, "need a context and W >= 1");
+    ewald_batch *b = new (std::nothrow) ewald_batch();
+    if (!b) return fail(c, EWALD_ERR_OOM);
+    b->ctx = c;
+    const SysDev &s = c->s;
+    BatchDev &d = b->b;
+    d.W = W;
+    const size_t slots = (size_t)s.n_runs * s.run_len;
+    std::vector<void *> &o = b->dev;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (!e) e = x; };
+    chk(dalloc(o, &d.u, (size_t)W * s.dim * s.mob_stride));
+    chk(dalloc(o, &d.rho, (size_t)W * slots));
+    chk(dalloc(o, &d.pend_k, W));
+    chk(dalloc(o, &d.pend_u, (size_t)W * 3));
+    chk(dalloc(o, &d.acc_count, W));
+    chk(dalloc(o, &d.resum_flag, W));
+    chk(dalloc(o, &d.part_real, (size_t)W * s.n_items));
+    chk(dalloc(o, &d.part_recip, (size_t)W * s.n_gchunks));
+    chk(dalloc(o, &d.e, W));
+    chk(dalloc(o, &d.comp, (size_t)W * 5));
+    chk(dalloc(o, &d.status, 1));
+    chk(dalloc(o, &b->d_k, W));
+    chk(dalloc(o, &b->d_rnew, (size_t)W * 3));
+    chk(dalloc(o, &b->d_de, W));
+    chk(dalloc(o, &b->d_acc, W));
+    size_t io = std::max({(size_t)W * s.n_mob * s.dim, (size_t)W * s.n_gh * 2, (size_t)W * 5});
+    b->d_io_bytes = io * sizeof(double);
+    chk(dalloc(o, &b->d_io, io));
+    if (!e) {
+        b->pin_bytes = b->d_io_bytes + (size_t)W * 8 + 64;
+        e = cudaMallocHost(&b->pin, b->pin_bytes);
+    }
+    if (!e) e = cudaMemsetAsync(d.status, 0, sizeof(int), c->stream);
+    if (!e) e = cudaMemsetAsync(d.pend_k, 0xff, W * sizeof(int), c->stream);
+    if (!e) e = cudaMemsetAsync(d.acc_count, 0, W * sizeof(int), c->stream);
+    if (!e) e = cudaMemsetAsync(d.resum_flag, 0, W, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) {
+        int code = (e == cudaErrorMemoryAllocation) ? EWALD_ERR_OOM : EWALD_ERR_CUDA;
+        ewald_batch_destroy(b);
+        cudaGetLastError();
+        return fail(c, code, cudaGetErrorString(e));
+    }
+    c->n_batches += 1;
+    b->counted = true;
+    *out = b;
+    return EWALD_OK;
+}
+
+void ewald_batch_destroy(ewald_batch *b) {
+    if (!b) return;
+    ewald_ctx *c = b->ctx;
+    const bool counted = b->counted;
+    if (c && c->stream) cudaStreamSynchronize(c->stream);
+    free_all(b->dev);
+    if (b->pin) cudaFreeHost(b->pin);
+    delete b;
+    if (counted) {
+        c->n_batches -= 1;
+        if (c->n_batches == 0 && c->destroy_pending) destroy_now(c);
+    }
+}
+
+int ewald_batch_set_positions(ewald_batch *b, const double *pos, int on_device) {
+    if (!b || !pos) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
+    ewald_ctx *c = b->ctx;
+    const double *src = pos;
+    int err = EWALD_OK;
+    if (!on_device) {
+        src = (const double *)copy_in(b, pos, (size_t)b->b.W * c->s.n_mob * c->s.dim * sizeof(double),
+                                      b->d_io, &err);
+        if (err) return err;
+    }
+    int e = timed(c, KT_INGEST, [&] { return launch_ingest(c->s, b->b, src, c->stream); });
+    if (e) return cuda_fail(c, (cudaError_t)e);
+    b->has_pos = true;
+    b->has_pending = false;
+    // rho(G) follows the new positions
+    e = timed(c, KT_RESUM, [&] { return launch_sfac(c->s, b->b, c->t.precision, c->cfg, nullptr, c->stream); });
+    if (e) return cuda_fail(c, (cudaError_t)e);
+    if (!on_device) return sync_status(b);
+    return EWALD_OK;
+}
+
+int ewald_batch_get_positions(ewald_batch *b, double *pos, int on_device) {
+    if (!ready(b) || !pos) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
+    ewald_ctx *c = b->ctx;
+    size_t n = (size_t)b->b.W * c->s.n_mob * c->s.dim * sizeof(double);
+    double *dst = on_device ? pos : b->d_io;
+    int e = launch_positions_out(c->s, b->b, dst, c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e);
+    if (on_device) return EWALD_OK;
+    return copy_out(b, pos, b->d_io, n, 0);
+}
+
+int ewald_batch_sync(ewald_batch *b) {
+    if (!b) return EWALD_ERR_ARG;
+    return sync_status(b);
+}
+
+int ewald_energy(ewald_batch *b, double *e_out, int on_device) {
+    if (!ready(b) || !e_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
+    int e = run_energy(b);
+    if (e) return e;
+    b->has_pending = false;
+    return copy_out(b, e_out, b->b.e, (size_t)b->b.W * sizeof(double), on_device);
+}
+
+int ewald_energy_components(ewald_batch *b, double *comp_out, int on_device) {
+    if (!ready(b) || !comp_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
+    int e = run_energy(b);
+    if (e) return e;
+    b->has_pending = false;
+    return copy_out(b, comp_out, b->b.comp, (size_t)b->b.W * 5 * sizeof(double), on_device);
+}
+
+int ewald_propose_move(ewald_batch *b, const int *k, const double *r_new, double *de_out, int on_device) {
+    if (!ready(b) || !k || !r_new || !de_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
+    ewald_ctx *c = b->ctx;
+    const int W = b->b.W, dim = c->s.dim;
+    const int *dk = k;
+    const double *dr = r_new;
+    if (!on_device) {
+        for (int w = 0; w < W; ++w) {
+            if (k[w] < 0 || k[w] >= c->s.n_mob) return fail(c, EWALD_ERR_ARG, "move index out of range");
+            for (int x = 0; x < dim; ++x)
+                if (!std::isfinite(r_new[(size_t)w * dim + x])) return fail(c, EWALD_ERR_ARG, "non-finite position");
+        }
+        // k and r_new share the pinned buffer: stage both, then one sync
+        char *pin = (char *)b->pin + 16;
+        size_t nk = (size_t)W * sizeof(int), nr = (size_t)W * dim * sizeof(double);
+        std::memcpy(pin, k, nk);
+        std::memcpy(pin + align16(nk), r_new, nr);
+        cudaError_t e = cudaMemcpyAsync(b->d_k, pin, nk, cudaMemcpyHostToDevice, c->stream);
+        if (!e) e = cudaMemcpyAsync(b->d_rnew, pin + align16(nk), nr, cudaMemcpyHostToDevice, c->stream);
+        if (e) return cuda_fail(c, e);
+        dk = b->d_k;
+        dr = b->d_rnew;
+    }
+    double *dde = on_device ? de_out : b->d_de;
+    int e = timed(c, KT_PROPOSE, [&] { return launch_propose(c->s, b->b, c->t.precision, c->cfg, dk, dr, dde, c->stream); });
+    if (e) return cuda_fail(c, (cudaError_t)e);
+    b->has_pending = true;
+    if (on_device) return EWALD_OK;
+    return copy_out(b, de_out, b->d_de, (size_t)W * sizeof(double), 0);
+}
+
+int ewald_accept_move(ewald_batch *b, const unsigned char *accept, int on_device) {
+    if (!ready(b) || !accept) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
+    ewald_ctx *c = b->ctx;
+    if (!b->has_pending) return fail(c, EWALD_ERR_NO_PROPOSAL, "no pending proposal");
+    const unsigned char *da = accept;
+    if (!on_device) {
+        int err;
+        da = (const unsigned char *)copy_in(b, accept, b->b.W, b->d_acc, &err);
+        if (err) return err;
+    }
+    const int p = c->t.precision;
+    int e = timed(c, KT_ACCEPT, [&] { return launch_accept(c->s, b->b, p, c->cfg, da, c->t.resum_every, c->stream); });
+    // rebuild rho(G) of the walkers that reached resum_every accepted moves
+    if (!e) e = timed(c, KT_RESUM, [&] { return launch_sfac(c->s, b->b, p, c->cfg, b->b.resum_flag, c->stream); });
+    if (e) return cuda_fail(c, (cudaError_t)e);
+    b->has_pending = false;
+    if (!on_device) return sync_status(b);
+    return EWALD_OK;
+}
+
+int ewald_resum(ewald_batch *b) {
+    if (!ready(b)) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
+    ewald_ctx *c = b->ctx;
+    int e = timed(c, KT_RESUM, [&] { return launch_sfac(c->s, b->b, c->t.precision, c->cfg, nullptr, c->stream); });
+    return e ? cuda_fail(c, (cudaError_t)e) : EWALD_OK;
+}
+
+int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device) {
+    if (!ready(b) || !rho_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
+    ewald_ctx *c = b->ctx;
+    double *dst = on_device ? rho_out : b->d_io;
+    int e = launch_rho_out(c->s, b->b, c->d_g2slot, dst, c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e);
+    if (on_device) return EWALD_OK;
+    return copy_out(b, rho_out, b->d_io, (size_t)b->b.W * c->s.n_gh * 2 * sizeof(double), 0);
+}
+
+int ewald_set_timing(ewald_ctx *c, int enable) {
+    if (!c) return EWALD_ERR_ARG;
+    if (c->timing && !enable) collect_timers(c);
+    c->timing = enable != 0;
+    return EWALD_OK;
+}
+
+int ewald_get_timing(ewald_ctx *c, double *ms, long long *launches) {
+    if (!c) return EWALD_ERR_ARG;
+    cudaError_t e = (cudaError_t)collect_timers(c);
+    for (int k = 0; k < KT_COUNT; ++k) {
+        if (ms) ms[k] = c->t_ms[k];
+        if (launches) launches[k] = c->t_n[k];
+        c->t_ms[k] = 0;
+        c->t_n[k] = 0;
+    }
+    return e ? cuda_fail(c, e) : EWALD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Internal declarations of the GB300 Ewald library (not part of the ABI).
+//
+// Data layout in device memory (per context = one periodic system):
+//   images   : candidate lattice vectors R (Cartesian), FP64 and FP32 copies
+//   cand     : per displacement cell, indices into images (uint16), padded
+//   runs     : G rows split into runs of <= run_len consecutive n1 (int4)
+//   gw       : weight of every G slot, 2 C f(G) (0 for padding slots)
+//   rho_fix  : fixed particles' rho(G) per slot
+// and per walker batch:
+//   u        : [W][dim][stride] fixed-point fractional coordinates (uint64,
+//              2^64 = one lattice period); FP32 kernels use the top 32 bits
+//   rho      : [W][run_len * n_runs] rho(G) (double2); slot = r * n_runs + run
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ewald.h"
+
+namespace ewald {
+
+constexpr int kRealWarps = 4;          // warps per real-space CTA
+constexpr int kRealThreads = 32 * kRealWarps;
+constexpr int kQueueCap = 64;          // per-warp queue of accepted (r^2, weight) terms
+constexpr int kSfacThreads = 256;      // threads (= runs) per structure-factor CTA
+constexpr int kMoveThreads = 256;      // threads per walker in propose / accept
+constexpr int kRunLen = 8;             // maximum G run length (compile-time)
+
+// FP64 image vector (x, y, z, unused), 32-byte aligned for two 16-byte loads.
+struct __align__(32) Img64 {
+    double x, y, z, w;
+};
+
+// Device-side error bits, OR-ed into the batch status word by kernels.
+enum : int { ST_COINCIDENT = 1, ST_BAD_INDEX = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
+
+// Per-system constants and table pointers; passed by value to kernels.
+struct SysDev {
+    int dim, n_mob, n_fix, mob_stride, fix_stride;
+    double A64[3][3];   // A[k][x] * 2^-64: Cartesian x of a uint64 fractional difference
+    float A32[3][3];    // A[k][x] * 2^-32 for the FP32 path
+    double A[3][3];     // lattice rows a_k
+    double Binv[3][3];  // f_k = sum_x Binv[k][x] r_x (fractional coordinates)
+    double alpha, rc2, coin2;
+    float alpha_f, rc2_f, coin2_f;
+    float alpha_lo_f, alpha2_f, alpha2_lo_f;  // alpha = alpha_f + alpha_lo_f, alpha^2 likewise
+    // real space
+    int n_img, sub_bits, cand_max;
+    const Img64 *img_d;
+    const float4 *img_f;
+    const unsigned short *cand;
+    const int *cand_len;
+    int tile, n_mob_tiles, n_items;  // pair tiles (T = tile) and items per walker
+    const int2 *items;               // (ti, tj); tj >= n_mob_tiles -> fixed tile tj - n_mob_tiles
+    // reciprocal space
+    int n_runs, run_len, n_gh, n_gchunks;
+    int n1max, n2max, n3max;
+    const int4 *runs;  // (n1 start, n2, n3, length)
+    const double *gw_d;
+    const float *gw_f;
+    const double2 *rho_fix;  // may be null
+    // charges and fixed particles
+    const double *q_mob, *q_fix;
+    const float *q_mob_f, *q_fix_f;
+    const unsigned long long *fix_u;  // [dim][fix_stride]
+    // constants (FP64)
+    double e_madR, e_self, e_bg, e_II;
+};
+
+// Per-batch device state.
+struct BatchDev {
+    int W;
+    unsigned long long *u;       // [W][dim][mob_stride]
+    double2 *rho;                // [W][slots]
+    int *pend_k;                 // [W], -1 = nothing pending
+    unsigned long long *pend_u;  // [W][3]
+    int *acc_count;              // [W]
+    unsigned char *resum_flag;   // [W]
+    double *part_real;           // [W][n_items]
+    double *part_recip;          // [W][n_gchunks]
+    double *e;                   // [W]
+    double *comp;                // [W][5]
+    int *status;                 // [1]
+};
+
+// Host-side tables built in FP64 by setup.cpp.
+struct HostTables {
+    int dim = 0, n_mob = 0, n_fix = 0, precision = 0, resum_every = 64;
+    double A[3][3] = {}, Ainv[3][3] = {}, B[3][3] = {};  // B rows = b_k, a_i.b_j = 2 pi d_ij
+    double volume = 0, alpha = 0, r_c = 0, g_c = 0;
+    std::vector<double> q_mob, q_fix, fix_pos;
+    // real space
+    std::vector<double> img;   // [n_img][3]
+    int sub_bits = 0, cand_max = 0;
+    std::vector<unsigned short> cand;  // [n_sub][cand_max]
+    std::vector<int> cand_len;         // [n_sub]
+    // reciprocal space
+    std::vector<int> gn;       // [n_gh][3] integer coordinates, storage order
+    std::vector<int> runs;     // [n_runs][4]
+    int run_len = kRunLen;
+    std::vector<double> gw;    // [run_len * n_runs]
+    std::vector<int> g2slot;   // [n_gh]
+    std::vector<double> rho_fix;  // [slots][2]
+    int n1max = 0, n2max = 0, n3max = 0;
+    // constants
+    double e_madR = 0, e_self = 0, e_bg = 0, e_II = 0;
+};
+
+// setup.cpp
+int build_tables(const ewald_desc *d, HostTables *t, std::string *why);
+int pick_subcells(HostTables *t, int max_bytes);
+
+// kernels.cu launchers (return cudaError_t as int)
+struct LaunchCfg {
+    int sm_count;
+    int real_grid;      // persistent grid of the real-space kernel
+    size_t real_smem, sfac_smem, move_smem;
+    int sfac_te;        // electrons per structure-factor tile
+};
+int configure_launch(const SysDev &s, int precision, LaunchCfg *cfg);
+int launch_ingest(const SysDev &s, const BatchDev &b, const double *pos, cudaStream_t st);
+int launch_positions_out(const SysDev &s, const BatchDev &b, double *pos, cudaStream_t st);
+int launch_real(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg,
+                cudaStream_t st);
+int launch_combine(const SysDev &s, const BatchDev &b, cudaStream_t st);
+int launch_sfac(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg,
+                const unsigned char *only, cudaStream_t st);
+int launch_propose(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg,
+                   const int *k, const double *r_new, double *de, cudaStream_t st);
+int launch_accept(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg,
+                  const unsigned char *acc, int resum_every, cudaStream_t st);
+
+// Kernel ids of the per-context timers (ewald_get_timing).
+enum { KT_INGEST = 0, KT_SFAC, KT_REAL, KT_COMBINE, KT_PROPOSE, KT_ACCEPT, KT_RESUM, KT_COUNT };
+int launch_rho_out(const SysDev &s, const BatchDev &b, const int *g2slot, double *out,
+                   cudaStream_t st);
+
+}  // namespace ewald

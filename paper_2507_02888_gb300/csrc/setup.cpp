@@ -1,0 +1,400 @@
+// Host set-up of a periodic system, in FP64 (paper Sec. 6.1: the Ewald
+// set-up tables are numerically sensitive and stay in double precision even
+// when the rest runs in single precision).
+//
+// Builds, from the lattice, the charges and alpha:
+//   - the reciprocal basis b_k (a_i . b_j = 2 pi delta_ij) and the volume;
+//   - the cutoffs (erfc(alpha r_c) = 1e-16; exp(-G^2/4alpha^2) = 1e-16 in 3D,
+//     erfc(G/2alpha) = 1e-16 in 2D) unless the caller gives them;
+//   - the G vectors of one half-space (one of each +-G pair), grouped in rows
+//     of consecutive n1 and split into runs for the structure-factor kernel,
+//     with weights 2 C f(G) (paper Eq. (3) and Eq. (5) at z = 0);
+//   - the lattice vectors that can bring a wrapped displacement inside r_c,
+//     and per displacement cell the short list of those that can for any
+//     displacement in that cell;
+//   - the position-independent energies: Madelung self-image, self,
+//     background and the real-space sum among fixed particles (Eqs. (2)-(6)),
+//     and the fixed particles' rho(G).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ewald_internal.h"
+
+namespace ewald {
+
+static const double kPi = 3.14159265358979323846;
+
+static bool all_finite(const double *p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// x with erfc(x) = y (0 < y < 1), Newton's method on log erfc.
+static double inverse_erfc(double y) {
+    double x = std::sqrt(-std::log(y));
+    for (int it = 0; it < 100; ++it) {
+        double e = std::erfc(x);
+        double g = std::log(e) - std::log(y);
+        double gp = -2.0 / std::sqrt(kPi) * std::exp(-x * x) / e;
+        double dx = g / gp;
+        x -= dx;
+        if (std::fabs(dx) < 1e-15 * std::fabs(x)) break;
+    }
+    return x;
+}
+
+static double norm_n(const double *v, int dim) {
+    double s = 0;
+    for (int k = 0; k < dim; ++k) s += v[k] * v[k];
+    return std::sqrt(s);
+}
+
+// Cartesian vector of integer or fractional lattice coordinates m: sum_k m_k a_k.
+static void lat_to_cart(const HostTables &t, const double *m, double *x) {
+    for (int y = 0; y < 3; ++y) x[y] = 0;
+    for (int y = 0; y < t.dim; ++y)
+        for (int k = 0; k < t.dim; ++k) x[y] += m[k] * t.A[k][y];
+}
+
+// Fractional coordinates f_k = b_k . r / 2pi.
+static void cart_to_frac(const HostTables &t, const double *r, double *f) {
+    for (int k = 0; k < t.dim; ++k) {
+        f[k] = 0;
+        for (int y = 0; y < t.dim; ++y) f[k] += t.Ainv[y][k] * r[y];
+    }
+}
+
+static int setup_lattice(HostTables *t, const double *lat, std::string *why) {
+    int dim = t->dim;
+    for (int i = 0; i < dim; ++i)
+        for (int k = 0; k < dim; ++k) t->A[i][k] = lat[i * dim + k];
+    double det;
+    if (dim == 3) {
+        double(*a)[3] = t->A;
+        double c[3][3];  // cofactors
+        c[0][0] = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+        c[0][1] = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+        c[0][2] = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+        c[1][0] = a[0][2] * a[2][1] - a[0][1] * a[2][2];
+        c[1][1] = a[0][0] * a[2][2] - a[0][2] * a[2][0];
+        c[1][2] = a[0][1] * a[2][0] - a[0][0] * a[2][1];
+        c[2][0] = a[0][1] * a[1][2] - a[0][2] * a[1][1];
+        c[2][1] = a[0][2] * a[1][0] - a[0][0] * a[1][2];
+        c[2][2] = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+        det = a[0][0] * c[0][0] + a[0][1] * c[0][1] + a[0][2] * c[0][2];
+        if (!(det > 0)) {
+            *why = "lattice is singular or left-handed (det <= 0)";
+            return EWALD_ERR_LATTICE;
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) t->Ainv[i][j] = c[j][i] / det;  // inverse = adj / det
+    } else {
+        double(*a)[3] = t->A;
+        det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+        if (!(det > 0)) {
+            *why = "lattice is singular or left-handed (det <= 0)";
+            return EWALD_ERR_LATTICE;
+        }
+        t->Ainv[0][0] = a[1][1] / det;
+        t->Ainv[0][1] = -a[0][1] / det;
+        t->Ainv[1][0] = -a[1][0] / det;
+        t->Ainv[1][1] = a[0][0] / det;
+    }
+    // scale-free conditioning check: reject nearly flat cells
+    double prod = 1;
+    for (int i = 0; i < dim; ++i) prod *= norm_n(t->A[i], dim);
+    if (det < 1e-10 * prod) {
+        *why = "lattice is (numerically) singular";
+        return EWALD_ERR_LATTICE;
+    }
+    t->volume = det;
+    for (int k = 0; k < dim; ++k)
+        for (int y = 0; y < dim; ++y) t->B[k][y] = 2 * kPi * t->Ainv[y][k];
+    return EWALD_OK;
+}
+
+// Largest |A^T f| over the corners of [-1/2, 1/2]^dim: the longest wrapped displacement.
+static double max_wrapped_norm(const HostTables &t) {
+    double best = 0;
+    for (int c = 0; c < (1 << t.dim); ++c) {
+        double f[3] = {0, 0, 0}, x[3];
+        for (int k = 0; k < t.dim; ++k) f[k] = (c >> k & 1) ? 0.5 : -0.5;
+        lat_to_cart(t, f, x);
+        best = std::max(best, norm_n(x, t.dim));
+    }
+    return best;
+}
+
+static void build_images(HostTables *t) {
+    int dim = t->dim;
+    double reach = t->r_c + max_wrapped_norm(*t);
+    int mb[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) mb[k] = (int)std::ceil(reach * norm_n(t->B[k], dim) / (2 * kPi));
+    struct Img { double r, x[3]; };
+    std::vector<Img> v;
+    for (int m0 = -mb[0]; m0 <= mb[0]; ++m0)
+        for (int m1 = -mb[1]; m1 <= mb[1]; ++m1)
+            for (int m2 = -mb[2]; m2 <= mb[2]; ++m2) {
+                double m[3] = {(double)m0, (double)m1, (double)m2}, x[3];
+                lat_to_cart(*t, m, x);
+                double r = norm_n(x, dim);
+                if (r < reach * (1 + 1e-9)) v.push_back({r, {x[0], x[1], x[2]}});
+            }
+    std::sort(v.begin(), v.end(), [](const Img &a, const Img &b) { return a.r < b.r; });
+    t->img.clear();
+    for (auto &i : v) t->img.insert(t->img.end(), {i.x[0], i.x[1], i.x[2]});
+}
+
+// Candidate lists for 2^bits displacement cells per axis.  Returns the
+// longest list.  A displacement cell is the parallelepiped [-1/2 + s/M,
+// -1/2 + (s+1)/M) of fractional coordinates; every point in it is within
+// d_max / M of its centre, so R can contribute only if |c + R| < r_c + d_max/M.
+static int build_cand(const HostTables &t, int bits, std::vector<unsigned short> *cand,
+                      std::vector<int> *len) {
+    int dim = t.dim, M = 1 << bits, n_sub = 1;
+    for (int k = 0; k < dim; ++k) n_sub *= M;
+    double rad = max_wrapped_norm(t) / M;
+    double lim = (t.r_c + rad) * (1 + 1e-9);
+    int n_img = (int)t.img.size() / 3;
+    std::vector<std::vector<unsigned short>> lists(n_sub);
+    int longest = 0;
+    for (int s = 0; s < n_sub; ++s) {
+        double f[3] = {0, 0, 0}, c[3];
+        for (int k = 0; k < dim; ++k) f[k] = -0.5 + (((s >> (k * bits)) & (M - 1)) + 0.5) / M;
+        lat_to_cart(t, f, c);
+        for (int i = 0; i < n_img; ++i) {
+            double x[3];
+            for (int y = 0; y < 3; ++y) x[y] = c[y] + t.img[3 * i + y];
+            if (norm_n(x, dim) < lim) lists[s].push_back((unsigned short)i);
+        }
+        longest = std::max(longest, (int)lists[s].size());
+    }
+    if (cand) {
+        cand->assign((size_t)n_sub * std::max(longest, 1), 0);
+        len->assign(n_sub, 0);
+        for (int s = 0; s < n_sub; ++s) {
+            (*len)[s] = (int)lists[s].size();
+            std::copy(lists[s].begin(), lists[s].end(), cand->begin() + (size_t)s * longest);
+        }
+    }
+    return longest;
+}
+
+// Choose the number of displacement cells: the shortest longest-list whose
+// table fits in max_bytes of shared memory.
+int pick_subcells(HostTables *t, int max_bytes) {
+    int best_bits = 0, best_len = 1 << 30;
+    int max_bits = t->dim == 3 ? 4 : 6;
+    for (int b = 0; b <= max_bits; ++b) {
+        int n_sub = 1 << (b * t->dim);
+        int L = build_cand(*t, b, nullptr, nullptr);
+        size_t bytes = (size_t)n_sub * L * 2 + (size_t)n_sub * 4;
+        if (bytes > (size_t)max_bytes) break;
+        if (L < best_len) {
+            best_len = L;
+            best_bits = b;
+        }
+    }
+    t->sub_bits = best_bits;
+    t->cand_max = build_cand(*t, best_bits, &t->cand, &t->cand_len);
+    return best_bits;
+}
+
+static void build_gvectors(HostTables *t) {
+    int dim = t->dim;
+    int nb[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) nb[k] = (int)std::ceil(t->g_c * norm_n(t->A[k], dim) / (2 * kPi));
+    struct Row { int n2, n3, lo, hi; };
+    std::vector<Row> rows;
+    int n3lo = 0, n3hi = dim == 3 ? nb[2] : 0;
+    for (int n3 = n3lo; n3 <= n3hi; ++n3)
+        for (int n2 = -nb[1]; n2 <= nb[1]; ++n2) {
+            if (n3 == 0 && n2 < 0) continue;  // half-space: first nonzero of (n3, n2, n1) > 0
+            int lo = 1 << 30, hi = -(1 << 30);
+            for (int n1 = -nb[0]; n1 <= nb[0]; ++n1) {
+                if (n3 == 0 && n2 == 0 && n1 <= 0) continue;
+                double G[3] = {0, 0, 0};
+                for (int y = 0; y < dim; ++y)
+                    G[y] = n1 * t->B[0][y] + n2 * t->B[1][y] + (dim == 3 ? n3 * t->B[2][y] : 0);
+                if (norm_n(G, dim) <= t->g_c) {
+                    lo = std::min(lo, n1);
+                    hi = std::max(hi, n1);
+                }
+            }
+            if (lo <= hi) rows.push_back({n2, n3, lo, hi});
+        }
+    // split rows into runs of <= run_len consecutive n1, lengths as equal as possible
+    t->runs.clear();
+    t->gn.clear();
+    t->n1max = t->n2max = t->n3max = 0;
+    for (auto &r : rows) {
+        int L = r.hi - r.lo + 1, nr = (L + t->run_len - 1) / t->run_len;
+        int start = r.lo;
+        for (int j = 0; j < nr; ++j) {
+            int len = L / nr + (j < L % nr ? 1 : 0);
+            t->runs.insert(t->runs.end(), {start, r.n2, r.n3, len});
+            start += len;
+        }
+        t->n1max = std::max(t->n1max, std::max(std::abs(r.lo), std::abs(r.hi)));
+        t->n2max = std::max(t->n2max, std::abs(r.n2));
+        t->n3max = std::max(t->n3max, std::abs(r.n3));
+    }
+    int n_runs = (int)t->runs.size() / 4;
+    int slots = n_runs * t->run_len;
+    t->gw.assign(slots, 0.0);
+    t->g2slot.clear();
+    double C = dim == 3 ? 2 * kPi / t->volume : kPi / t->volume;
+    for (int run = 0; run < n_runs; ++run) {
+        const int *rn = &t->runs[4 * run];
+        for (int j = 0; j < rn[3]; ++j) {
+            int n[3] = {rn[0] + j, rn[1], rn[2]};
+            double G[3] = {0, 0, 0};
+            for (int y = 0; y < dim; ++y)
+                for (int k = 0; k < dim; ++k) G[y] += n[k] * t->B[k][y];
+            double g = norm_n(G, dim);
+            double f = dim == 3 ? std::exp(-g * g / (4 * t->alpha * t->alpha)) / (g * g)
+                                : std::erfc(g / (2 * t->alpha)) / g;
+            int slot = j * n_runs + run;
+            t->gw[slot] = 2 * C * f;  // half-space: +G and -G give equal terms
+            t->g2slot.push_back(slot);
+            for (int k = 0; k < dim; ++k) t->gn.push_back(n[k]);
+        }
+    }
+}
+
+static void build_constants(HostTables *t) {
+    int dim = t->dim;
+    double q2 = 0, Q = 0;
+    for (double q : t->q_mob) { q2 += q * q; Q += q; }
+    for (double q : t->q_fix) { q2 += q * q; Q += q; }
+    t->e_self = -t->alpha / std::sqrt(kPi) * q2;
+    t->e_bg = dim == 3 ? -kPi * Q * Q / (2 * t->volume * t->alpha * t->alpha)
+                       : -std::sqrt(kPi) * Q * Q / (t->volume * t->alpha);
+    // Madelung self-image sum over R != 0 inside r_c: the image list covers |R| < r_c.
+    int n_img = (int)t->img.size() / 3;
+    double smad = 0;
+    for (int i = 0; i < n_img; ++i) {
+        double r = norm_n(&t->img[3 * i], dim);
+        if (r > 0 && r < t->r_c) smad += std::erfc(t->alpha * r) / r;
+    }
+    t->e_madR = 0.5 * q2 * smad;
+    // fixed-fixed real-space pairs, wrapped displacement + candidate images
+    double eII = 0;
+    for (int I = 0; I < t->n_fix; ++I)
+        for (int J = I + 1; J < t->n_fix; ++J) {
+            double d[3] = {0, 0, 0}, f[3], dw[3];
+            for (int y = 0; y < dim; ++y) d[y] = t->fix_pos[I * dim + y] - t->fix_pos[J * dim + y];
+            cart_to_frac(*t, d, f);
+            for (int k = 0; k < dim; ++k) f[k] -= std::floor(f[k] + 0.5);
+            lat_to_cart(*t, f, dw);
+            double s = 0;
+            for (int i = 0; i < n_img; ++i) {
+                double x[3];
+                for (int y = 0; y < 3; ++y) x[y] = dw[y] + t->img[3 * i + y];
+                double r = norm_n(x, dim);
+                if (r < t->r_c && r > 0) s += std::erfc(t->alpha * r) / r;
+            }
+            eII += t->q_fix[I] * t->q_fix[J] * s;
+        }
+    t->e_II = eII;
+    // fixed particles' rho(G) per slot: sum_I q_I exp(2 pi i n . f_I)
+    int n_runs = (int)t->runs.size() / 4;
+    t->rho_fix.assign((size_t)n_runs * t->run_len * 2, 0.0);
+    if (t->n_fix == 0) return;
+    std::vector<double> fr(t->n_fix * 3, 0.0);
+    for (int I = 0; I < t->n_fix; ++I) cart_to_frac(*t, &t->fix_pos[I * dim], &fr[3 * I]);
+    for (int run = 0; run < n_runs; ++run) {
+        const int *rn = &t->runs[4 * run];
+        for (int j = 0; j < rn[3]; ++j) {
+            int n[3] = {rn[0] + j, rn[1], rn[2]};
+            double re = 0, im = 0;
+            for (int I = 0; I < t->n_fix; ++I) {
+                double ph = 0;
+                for (int k = 0; k < dim; ++k) ph += n[k] * fr[3 * I + k];
+                ph = 2 * kPi * (ph - std::floor(ph));
+                re += t->q_fix[I] * std::cos(ph);
+                im += t->q_fix[I] * std::sin(ph);
+            }
+            int slot = j * n_runs + run;
+            t->rho_fix[2 * slot] = re;
+            t->rho_fix[2 * slot + 1] = im;
+        }
+    }
+}
+
+int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
+    if (!d) { *why = "desc is NULL"; return EWALD_ERR_ARG; }
+    if (d->dim != 2 && d->dim != 3) { *why = "dim must be 2 or 3"; return EWALD_ERR_ARG; }
+    if (!d->lattice) { *why = "lattice is NULL"; return EWALD_ERR_ARG; }
+    if (d->n_mobile < 1 || !d->mobile_charge) { *why = "need n_mobile >= 1 and charges"; return EWALD_ERR_ARG; }
+    if (d->n_fixed < 0 || (d->n_fixed > 0 && (!d->fixed_pos || !d->fixed_charge))) {
+        *why = "bad fixed particles";
+        return EWALD_ERR_ARG;
+    }
+    if (d->n_mobile > (1 << 20) || d->n_fixed > (1 << 20)) { *why = "too many particles"; return EWALD_ERR_ARG; }
+    if (d->precision != EWALD_FP64 && d->precision != EWALD_MIXED) { *why = "bad precision"; return EWALD_ERR_ARG; }
+    int dim = d->dim;
+    if (!all_finite(d->lattice, dim * dim) || !all_finite(d->mobile_charge, d->n_mobile) ||
+        (d->n_fixed && (!all_finite(d->fixed_pos, (size_t)d->n_fixed * dim) ||
+                        !all_finite(d->fixed_charge, d->n_fixed))) ||
+        !std::isfinite(d->gamma) || !std::isfinite(d->g_cutoff) || !std::isfinite(d->r_cutoff)) {
+        *why = "non-finite input";
+        return EWALD_ERR_ARG;
+    }
+    t->dim = dim;
+    t->n_mob = d->n_mobile;
+    t->n_fix = d->n_fixed;
+    t->precision = d->precision;
+    t->resum_every = d->resum_every > 0 ? d->resum_every : 64;
+    t->q_mob.assign(d->mobile_charge, d->mobile_charge + d->n_mobile);
+    t->q_fix.assign(d->fixed_charge, d->fixed_charge + d->n_fixed);
+    t->fix_pos.assign(d->fixed_pos, d->fixed_pos + (size_t)d->n_fixed * dim);
+    int st = setup_lattice(t, d->lattice, why);
+    if (st) return st;
+
+    const double tol = 1e-16;
+    double x_r = inverse_erfc(tol);
+    if (d->gamma > 0) {
+        t->alpha = d->gamma;
+    } else {
+        // Balanced alpha: real-space and reciprocal work of the same order, with
+        // N_G ~ sqrt(K N) reciprocal vectors (K from the trade-off between the
+        // image count inside r_c and the G count inside g_c at 1e-16).
+        double n = d->n_mobile + d->n_fixed;
+        if (dim == 3) {
+            double ng = std::sqrt(2.56e4 * n);
+            double gc = std::cbrt(ng * 6 * kPi * kPi / t->volume);
+            t->alpha = gc / (2 * std::sqrt(-std::log(tol)));
+        } else {
+            double ng = std::sqrt(1.19e3 * n);
+            double gc = std::sqrt(ng * 4 * kPi / t->volume);
+            t->alpha = gc / (2 * x_r);
+        }
+    }
+    t->r_c = d->r_cutoff > 0 ? d->r_cutoff : x_r / t->alpha;
+    t->g_c = d->g_cutoff > 0 ? d->g_cutoff
+                             : (dim == 3 ? 2 * t->alpha * std::sqrt(-std::log(tol)) : 2 * t->alpha * x_r);
+    // guard against cutoffs that would need absurd tables
+    double Lc = std::pow(t->volume, 1.0 / dim);
+    if (t->r_c > 64 * Lc || t->g_c * Lc / (2 * kPi) > 256) {
+        *why = "cutoff too large for the cell";
+        return EWALD_ERR_ARG;
+    }
+    build_images(t);
+    if (t->img.size() / 3 > 4000) {
+        *why = "real-space cutoff needs more than 4000 candidate images";
+        return EWALD_ERR_ARG;
+    }
+    pick_subcells(t, 24 * 1024);
+    build_gvectors(t);
+    if (t->runs.empty()) {
+        *why = "no G vector inside the cutoff";
+        return EWALD_ERR_ARG;
+    }
+    build_constants(t);
+    return EWALD_OK;
+}
+
+}  // namespace ewald

@@ -1,0 +1,299 @@
+"""Thin ctypes binding of libewald_gb300.so (C ABI in include/ewald.h).
+
+This module only marshals arguments: every step of the computation runs in
+the library's CUDA kernels.  Arrays may be NumPy arrays (host memory) or
+CUDA torch tensors (device memory, passed by pointer with on_device=1 and
+accessed on the context's stream).  The library must be built
+(``paper_2507_02888_gb300.build``); loading fails loudly when it is not.
+"""
+import atexit
+import ctypes
+import os
+import weakref
+
+import numpy as np
+
+from . import build as _build
+
+EWALD_FP64, EWALD_MIXED = 0, 1
+ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_LATTICE", 3: "ERR_COINCIDENT", 4: "ERR_NO_PROPOSAL",
+             5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
+
+_c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class EwaldError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s (%d)%s" % (ERR_NAMES.get(code, "?"), code, (": " + what) if what else ""))
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("dim", _c_int), ("lattice", _dp), ("n_mobile", _c_int), ("mobile_charge", _dp),
+                ("n_fixed", _c_int), ("fixed_pos", _dp), ("fixed_charge", _dp), ("gamma", _c_double),
+                ("g_cutoff", _c_double), ("r_cutoff", _c_double), ("precision", _c_int),
+                ("resum_every", _c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dim", _c_int), ("n_mobile", _c_int), ("n_fixed", _c_int), ("precision", _c_int),
+                ("alpha", _c_double), ("r_cutoff", _c_double), ("g_cutoff", _c_double),
+                ("volume", _c_double), ("n_g_half", _c_int), ("n_images", _c_int),
+                ("subcell_bits", _c_int), ("max_candidates", _c_int), ("n_runs", _c_int),
+                ("run_len", _c_int), ("e_madelung", _c_double), ("e_self", _c_double),
+                ("e_background", _c_double), ("e_fixed_real", _c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_live_batches = weakref.WeakSet()
+_live_contexts = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    """Free library objects while the CUDA runtime is still up (interpreter exit)."""
+    for b in list(_live_batches):
+        b.close()
+    for c in list(_live_contexts):
+        c.close()
+
+# (name, restype, argtypes) of every entry point declared in include/ewald.h
+SIGNATURES = [
+    ("ewald_create", _c_int, [ctypes.POINTER(Desc), _vp, ctypes.POINTER(_vp)]),
+    ("ewald_destroy", None, [_vp]),
+    ("ewald_get_info", _c_int, [_vp, ctypes.POINTER(Info)]),
+    ("ewald_get_gvectors", _c_int, [_vp, _vp]),
+    ("ewald_last_error", _c_int, [_vp]),
+    ("ewald_strerror", ctypes.c_char_p, [_c_int]),
+    ("ewald_batch_create", _c_int, [_vp, _c_int, ctypes.POINTER(_vp)]),
+    ("ewald_batch_destroy", None, [_vp]),
+    ("ewald_batch_set_positions", _c_int, [_vp, _vp, _c_int]),
+    ("ewald_batch_get_positions", _c_int, [_vp, _vp, _c_int]),
+    ("ewald_batch_sync", _c_int, [_vp]),
+    ("ewald_energy", _c_int, [_vp, _vp, _c_int]),
+    ("ewald_energy_components", _c_int, [_vp, _vp, _c_int]),
+    ("ewald_propose_move", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
+    ("ewald_accept_move", _c_int, [_vp, _vp, _c_int]),
+    ("ewald_resum", _c_int, [_vp]),
+    ("ewald_batch_get_rho", _c_int, [_vp, _vp, _c_int]),
+    ("ewald_set_timing", _c_int, [_vp, _c_int]),
+    ("ewald_get_timing", _c_int, [_vp, _vp, _vp]),
+]
+
+KERNELS = ["ingest", "sfac", "real", "combine", "propose", "accept", "resum"]
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load the shared library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libewald_gb300.so is not built; run python -m paper_2507_02888_gb300.build")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code, ctx=None):
+    if code != 0:
+        raise EwaldError(code, _lib.ewald_strerror(code).decode())
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def _is_dev(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x):
+    """(pointer, on_device) of a NumPy array or a CUDA torch tensor."""
+    if _is_dev(x):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), 1
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous")
+    return ctypes.c_void_p(x.ctypes.data), 0
+
+
+class Context:
+    """One periodic system: cell, charges, alpha, cutoffs and precision."""
+
+    def __init__(self, dim, lattice, mobile_charge, fixed_pos=None, fixed_charge=None, alpha=0.0,
+                 g_cutoff=0.0, r_cutoff=0.0, precision="fp64", resum_every=0, stream=None):
+        lib = load()
+        self.dim = int(dim)
+        self._lat = _f64(lattice, self.dim * self.dim)
+        self._qm = _f64(mobile_charge)
+        nf = 0 if fixed_charge is None else len(fixed_charge)
+        self._fp = _f64(fixed_pos if nf else np.zeros(1))
+        self._fq = _f64(fixed_charge if nf else np.zeros(1))
+        prec = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED}.get(precision, precision)
+        d = Desc(self.dim, self._lat.ctypes.data_as(_dp), len(self._qm), self._qm.ctypes.data_as(_dp),
+                 nf, self._fp.ctypes.data_as(_dp), self._fq.ctypes.data_as(_dp), float(alpha),
+                 float(g_cutoff), float(r_cutoff), int(prec), int(resum_every))
+        h = _vp()
+        if stream is None:
+            st = None
+        elif isinstance(stream, int):
+            st = _vp(stream)
+        else:
+            st = _vp(stream.cuda_stream)
+        _check(lib.ewald_create(ctypes.byref(d), st, ctypes.byref(h)))
+        self._h = h
+        _live_contexts.add(self)
+        self.n_mobile = len(self._qm)
+        self.n_fixed = nf
+        self.precision = prec
+
+    def info(self):
+        i = Info()
+        _check(_lib.ewald_get_info(self._h, ctypes.byref(i)))
+        return i.as_dict()
+
+    def gvectors(self):
+        n = self.info()["n_g_half"]
+        out = np.zeros((n, self.dim), dtype=np.int32)
+        _check(_lib.ewald_get_gvectors(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_timing(self, enable=True):
+        _check(_lib.ewald_set_timing(self._h, int(bool(enable))))
+
+    def timing(self):
+        """{kernel: (device ms, launches)} accumulated since the last call."""
+        ms = np.zeros(len(KERNELS))
+        n = np.zeros(len(KERNELS), dtype=np.int64)
+        _check(_lib.ewald_get_timing(self._h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(n.ctypes.data)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+    def last_error(self):
+        return _lib.ewald_last_error(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ewald_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """W walkers of a Context with device-resident positions and rho(G)."""
+
+    def __init__(self, ctx, n_walkers):
+        self.ctx = ctx
+        self.W = int(n_walkers)
+        h = _vp()
+        _check(_lib.ewald_batch_create(ctx._h, self.W, ctypes.byref(h)))
+        self._h = h
+        _live_batches.add(self)
+
+    # -- positions
+    def set_positions(self, pos):
+        if not _is_dev(pos):
+            pos = _f64(pos, self.W * self.ctx.n_mobile * self.ctx.dim)
+        p, dev = _ptr(pos)
+        _check(_lib.ewald_batch_set_positions(self._h, p, dev))
+
+    def get_positions(self, out=None):
+        if out is None:
+            out = np.zeros((self.W, self.ctx.n_mobile, self.ctx.dim))
+        p, dev = _ptr(out)
+        _check(_lib.ewald_batch_get_positions(self._h, p, dev))
+        return out
+
+    # -- energies
+    def energy(self, out=None):
+        if out is None:
+            out = np.zeros(self.W)
+        p, dev = _ptr(out)
+        _check(_lib.ewald_energy(self._h, p, dev))
+        return out
+
+    def components(self, out=None):
+        if out is None:
+            out = np.zeros((self.W, 5))
+        p, dev = _ptr(out)
+        _check(_lib.ewald_energy_components(self._h, p, dev))
+        return out
+
+    # -- moves
+    def propose(self, k, r_new, out=None):
+        if _is_dev(k):
+            if out is None:
+                import torch
+                out = torch.empty(self.W, dtype=torch.float64, device=k.device)
+        else:
+            k = np.ascontiguousarray(np.asarray(k, dtype=np.int32))
+            r_new = _f64(r_new, self.W * self.ctx.dim)
+            if out is None:
+                out = np.zeros(self.W)
+        pk, dev = _ptr(k)
+        pr, _ = _ptr(r_new)
+        po, _ = _ptr(out)
+        _check(_lib.ewald_propose_move(self._h, pk, pr, po, dev))
+        return out
+
+    def accept(self, accept):
+        if not _is_dev(accept):
+            accept = np.ascontiguousarray(np.asarray(accept, dtype=np.uint8))
+        p, dev = _ptr(accept)
+        _check(_lib.ewald_accept_move(self._h, p, dev))
+
+    def resum(self):
+        _check(_lib.ewald_resum(self._h))
+
+    def rho(self, out=None):
+        n = self.ctx.info()["n_g_half"]
+        if out is None:
+            out = np.zeros((self.W, n, 2))
+        p, dev = _ptr(out)
+        _check(_lib.ewald_batch_get_rho(self._h, p, dev))
+        return out
+
+    def sync(self):
+        _check(_lib.ewald_batch_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ewald_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def context_for(workload, precision="fp64", stream=None, **kw):
+    """Context for a workload dict from paper_2507_02888_gb300.inputs."""
+    w = workload
+    return Context(w["dim"], w["lattice"], w["q"], w["fixed_pos"] if len(w["fixed_q"]) else None,
+                   w["fixed_q"] if len(w["fixed_q"]) else None, alpha=w["alpha"], precision=precision,
+                   stream=stream, **kw)
