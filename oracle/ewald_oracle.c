@@ -65,6 +65,23 @@ typedef struct {
     double vol;     /* |volume| (3D) or |area| (2D) */
 } cell_t;
 
+/*
+ * Compensated (Neumaier) running sum.  The long sums of the energy (over
+ * ~5e5 particle pairs, over thousands of G vectors) would otherwise carry a
+ * rounding error of ~1e-10 of their size, above the 1e-12 relative parity
+ * gate; compensation keeps the oracle's own error near one rounding.
+ */
+typedef struct { double s, c; } ksum_t;
+
+static void kadd(ksum_t *k, double x) {
+    double t = k->s + x;
+    if (fabs(k->s) >= fabs(x)) k->c += (k->s - t) + x;
+    else k->c += (x - t) + k->s;
+    k->s = t;
+}
+
+static double kval(const ksum_t *k) { return k->s + k->c; }
+
 static double dot(int dim, const double *x, const double *y) {
     double s = 0.0;
     for (int k = 0; k < dim; ++k) s += x[k] * y[k];
@@ -200,7 +217,7 @@ typedef struct {
     int dim, n;
     const double *pos, *q;
     double alpha;
-    double sum;
+    ksum_t sum;
     long count;
 } recip_ctx;
 
@@ -214,7 +231,7 @@ static void visit_recip(const double *G, double g, const int *nvec, void *vctx) 
         re += r->q[i] * cos(ph);
         im += r->q[i] * sin(ph);
     }
-    r->sum += recip_weight(r->dim, g, r->alpha) * (re * re + im * im);
+    kadd(&r->sum, recip_weight(r->dim, g, r->alpha) * (re * re + im * im));
     r->count += 1;
 }
 
@@ -230,7 +247,7 @@ static void visit_recip_pairs(const double *G, double g, const int *nvec, void *
                 d[y] = r->pos[(size_t)i * r->dim + y] - r->pos[(size_t)j * r->dim + y];
             s += r->q[i] * r->q[j] * cos(dot(r->dim, G, d));
         }
-    r->sum += recip_weight(r->dim, g, r->alpha) * s;
+    kadd(&r->sum, recip_weight(r->dim, g, r->alpha) * s);
     r->count += 1;
 }
 
@@ -257,15 +274,16 @@ int oracle_energy(int dim, const double *lattice, int n, const double *pos, cons
     cell_t c;
     if ((st = make_cell(dim, lattice, &c))) return st;
 
-    double e_real = 0.0;
+    ksum_t e_real_sum = {0.0, 0.0};
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
             double d[3] = {0, 0, 0}, s;
             for (int y = 0; y < dim; ++y)
                 d[y] = pos[(size_t)i * dim + y] - pos[(size_t)j * dim + y];
             if ((st = image_sum(&c, d, alpha, r_c, 0, &s))) return st;
-            e_real += q[i] * q[j] * s;
+            kadd(&e_real_sum, q[i] * q[j] * s);
         }
+    double e_real = kval(&e_real_sum);
 
     double zero[3] = {0, 0, 0}, smad, q2 = 0.0, qsum = 0.0;
     if ((st = image_sum(&c, zero, alpha, r_c, 1, &smad))) return st;
@@ -275,9 +293,9 @@ int oracle_energy(int dim, const double *lattice, int n, const double *pos, cons
     }
     double e_madR = 0.5 * q2 * smad;
 
-    recip_ctx rc = {dim, n, pos, q, alpha, 0.0, 0};
+    recip_ctx rc = {dim, n, pos, q, alpha, {0.0, 0.0}, 0};
     for_each_g(&c, g_c, visit_recip, &rc);
-    double e_recip = recip_prefactor(&c) * rc.sum;
+    double e_recip = recip_prefactor(&c) * kval(&rc.sum);
 
     double e_self = -alpha / sqrt(M_PI) * q2;
     double e_bg = dim == 3 ? -M_PI * qsum * qsum / (2.0 * c.vol * alpha * alpha)
@@ -304,7 +322,7 @@ typedef struct {
     int dim, n, k;
     const double *pos, *q, *r_new;
     double alpha;
-    double sum;
+    ksum_t sum;
 } move_ctx;
 
 static void visit_move(const double *G, double g, const int *nvec, void *vctx) {
@@ -322,7 +340,7 @@ static void visit_move(const double *G, double g, const int *nvec, void *vctx) {
     double dim_ = m->q[m->k] * (sin(ph_new) - sin(ph_old));
     double after = (re + dre) * (re + dre) + (im + dim_) * (im + dim_);
     double before = re * re + im * im;
-    m->sum += recip_weight(m->dim, g, m->alpha) * (after - before);
+    kadd(&m->sum, recip_weight(m->dim, g, m->alpha) * (after - before));
 }
 
 int oracle_delta_e(int dim, const double *lattice, int n, const double *pos, const double *q,
@@ -334,7 +352,7 @@ int oracle_delta_e(int dim, const double *lattice, int n, const double *pos, con
     cell_t c;
     if ((st = make_cell(dim, lattice, &c))) return st;
 
-    double d_real = 0.0;
+    ksum_t d_real = {0.0, 0.0};
     for (int j = 0; j < n; ++j) {
         if (j == k) continue;
         double dn[3] = {0, 0, 0}, dold[3] = {0, 0, 0}, sn, so;
@@ -344,11 +362,11 @@ int oracle_delta_e(int dim, const double *lattice, int n, const double *pos, con
         }
         if ((st = image_sum(&c, dn, alpha, r_c, 0, &sn))) return st;
         if ((st = image_sum(&c, dold, alpha, r_c, 0, &so))) return st;
-        d_real += q[k] * q[j] * (sn - so);
+        kadd(&d_real, q[k] * q[j] * (sn - so));
     }
-    move_ctx mc = {dim, n, k, pos, q, r_new, alpha, 0.0};
+    move_ctx mc = {dim, n, k, pos, q, r_new, alpha, {0.0, 0.0}};
     for_each_g(&c, g_c, visit_move, &mc);
-    *de = d_real + recip_prefactor(&c) * mc.sum;
+    *de = kval(&d_real) + recip_prefactor(&c) * kval(&mc.sum);
     return ORC_OK;
 }
 
@@ -385,9 +403,9 @@ int oracle_recip_pairsum(int dim, const double *lattice, int n, const double *po
     cell_t c;
     int st = make_cell(dim, lattice, &c);
     if (st) return st;
-    recip_ctx rc = {dim, n, pos, q, alpha, 0.0, 0};
+    recip_ctx rc = {dim, n, pos, q, alpha, {0.0, 0.0}, 0};
     for_each_g(&c, g_c, visit_recip_pairs, &rc);
-    *e_recip = recip_prefactor(&c) * rc.sum;
+    *e_recip = recip_prefactor(&c) * kval(&rc.sum);
     return ORC_OK;
 }
 
@@ -395,7 +413,7 @@ int oracle_recip_pairsum(int dim, const double *lattice, int n, const double *po
 long oracle_gcount(int dim, const double *lattice, double g_c) {
     cell_t c;
     if (make_cell(dim, lattice, &c)) return -1;
-    recip_ctx rc = {dim, 0, NULL, NULL, 1.0, 0.0, 0};
+    recip_ctx rc = {dim, 0, NULL, NULL, 1.0, {0.0, 0.0}, 0};
     for_each_g(&c, g_c, visit_count, &rc);
     return rc.count;
 }
