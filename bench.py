@@ -153,7 +153,8 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-REAL_SOURCES = ["paper_2507_02888_gb300/csrc/energy_kernels.cu", "paper_2507_02888_gb300/csrc/device_common.cuh"]
+REAL_SOURCES = ["paper_2507_02888_gb300/csrc/energy_kernels.cu", "paper_2507_02888_gb300/csrc/energy_items.cuh",
+                "paper_2507_02888_gb300/csrc/device_common.cuh"]
 
 
 def profiled_traffic(workload, precision):

@@ -144,6 +144,26 @@ int ewald_resum(ewald_batch *b);
  * of ewald_get_gvectors; includes the fixed particles' contribution. */
 int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device);
 
+/* Batched form: walkers of several batches - of different systems (N,
+ * cell, dimension 2 or 3, charges), all of one precision - evaluated by one
+ * persistent kernel launch per call.  The work items (walker x chunk of G
+ * runs, walker x pair tile) are ordered longest first at creation and taken
+ * by the CTAs from an atomic counter; the CTA that finishes a walker's last
+ * item adds up its energy in a fixed order, so every result equals the
+ * single-batch ewald_energy of that walker bit for bit.  The launch is
+ * captured once in a CUDA graph and replayed by every call.  The batches
+ * must keep their positions set and outlive the multi object; their
+ * contexts' streams are ordered with the multi's own stream by events.
+ * (Paper Sec. 5.1 splits the Ewald sum into independent real- and
+ * reciprocal-space loops; here those loops of many systems share one
+ * launch.) */
+typedef struct ewald_multi ewald_multi;
+int ewald_multi_create(ewald_batch *const *batches, int n_batches, ewald_multi **out);
+/* e_out[sum_b W_b]: energies of every walker, batches in creation order.
+ * Also rebuilds every walker's rho(G), like ewald_energy. */
+int ewald_multi_energy(ewald_multi *m, double *e_out, int on_device);
+void ewald_multi_destroy(ewald_multi *m);
+
 /* Kernel timers of a context (in the spirit of the paper's per-subroutine
  * timers, Sec. 3.2).  When enabled, every kernel the context launches is
  * bracketed by CUDA events on its stream.  ewald_get_timing synchronises

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "device_common.cuh"
+#include "multi.h"
 
 using namespace ewald;
 
@@ -103,6 +104,7 @@ int build_device(ewald_ctx *c) {
             s.A[k][x] = t.A[k][x];
             s.A64[k][x] = std::ldexp(t.A[k][x], -64);
             s.A32[k][x] = (float)std::ldexp(t.A[k][x], -32);
+            s.A32lo[k][x] = (float)(std::ldexp(t.A[k][x], -32) - (double)s.A32[k][x]);
             s.Binv[k][x] = t.Ainv[x][k];
         }
     s.alpha = t.alpha;
@@ -118,12 +120,15 @@ int build_device(ewald_ctx *c) {
     cudaError_t e;
     // images
     int n_img = (int)t.img.size() / 3;
-    std::vector<Img64> imd(n_img);
-    std::vector<float4> imf(n_img);
+    std::vector<Img64> imd(n_img + 1);
+    std::vector<float4> imf(n_img + 1);
     for (int i = 0; i < n_img; ++i) {
         imd[i] = Img64{t.img[3 * i], t.img[3 * i + 1], t.img[3 * i + 2], 0.0};
         imf[i] = make_float4((float)t.img[3 * i], (float)t.img[3 * i + 1], (float)t.img[3 * i + 2], 0.f);
     }
+    // sentinel that pads the candidate lists: |d + R|^2 ~ 3e36 never passes the cutoff
+    imd[n_img] = Img64{1e18, 1e18, 1e18, 0.0};
+    imf[n_img] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
     s.n_img = n_img;
     s.sub_bits = t.sub_bits;
     s.cand_max = t.cand_max;
@@ -612,6 +617,206 @@ int ewald_get_timing(ewald_ctx *c, double *ms, long long *launches) {
         c->t_n[k] = 0;
     }
     return e ? cuda_fail(c, e) : EWALD_OK;
+}
+
+// ------------------------------------------------------------------ multi
+
+struct ewald_multi {
+    std::vector<ewald_batch *> batches;
+    std::vector<ewald_ctx *> ctxs;        // distinct contexts, in first-use order
+    int precision = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<void *> dev;
+    MultiDev m{};
+    size_t smem = 0;
+    int grid = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev_out = nullptr;
+    std::vector<cudaEvent_t> ev_in;
+    double *pin = nullptr;
+};
+
+namespace {
+
+// Estimated cost of an item, for longest-first ordering (relative units:
+// one electron-G term = 1; a pair costs its candidate tests and its terms).
+double item_cost(const SysDev &s, int kind, int sub) {
+    if (kind == kItemSfac) {
+        int runs = std::min(kSfacThreads, s.n_runs - sub * kSfacThreads);  // run lengths vary; bound
+        return (double)runs * s.run_len * s.n_mob;
+    }
+    return 1.0;  // scaled by the caller
+}
+
+}  // namespace
+
+int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
+    if (!out) return EWALD_ERR_ARG;
+    *out = nullptr;
+    if (!batches || n < 1) return EWALD_ERR_ARG;
+    ewald_multi *m = new (std::nothrow) ewald_multi();
+    if (!m) return EWALD_ERR_OOM;
+    std::vector<SysDev> sys;
+    std::vector<BatchDev> bat;
+    std::vector<int> bat_sys, wbase;
+    int nw = 0;
+    for (int i = 0; i < n; ++i) {
+        ewald_batch *b = batches[i];
+        if (!b || !b->ctx || !b->has_pos) {
+            delete m;
+            return EWALD_ERR_ARG;
+        }
+        if (i == 0) m->precision = b->ctx->t.precision;
+        if (b->ctx->t.precision != m->precision) {
+            delete m;
+            return EWALD_ERR_ARG;
+        }
+        int si = -1;
+        for (size_t k = 0; k < m->ctxs.size(); ++k)
+            if (m->ctxs[k] == b->ctx) si = (int)k;
+        if (si < 0) {
+            si = (int)m->ctxs.size();
+            m->ctxs.push_back(b->ctx);
+            sys.push_back(b->ctx->s);
+        }
+        m->batches.push_back(b);
+        bat.push_back(b->b);
+        bat_sys.push_back(si);
+        wbase.push_back(nw);
+        nw += b->b.W;
+    }
+    // work items, longest first
+    struct It { double cost; int4 d; };
+    std::vector<It> items;
+    for (int i = 0; i < n; ++i) {
+        const SysDev &s = sys[bat_sys[i]];
+        const double ipp = s.dim == 3 ? 4.18879 * std::pow(std::sqrt(s.rc2), 3) : 3.14159 * s.rc2;
+        const double vol = m->ctxs[bat_sys[i]]->t.volume;
+        const double pair_cost = 3.0 * s.cand_max + 6.0 * ipp / vol;
+        const std::vector<int> &rt = m->ctxs[bat_sys[i]]->t.runs;
+        (void)rt;
+        for (int w = 0; w < bat[i].W; ++w) {
+            for (int c = 0; c < s.n_gchunks; ++c)
+                items.push_back({item_cost(s, kItemSfac, c), make_int4(kItemSfac, i, w, c)});
+            for (int p = 0; p < s.n_items; ++p) {
+                // pairs of the tile pair (ragged tails and diagonal triangles)
+                const HostTables &t = m->ctxs[bat_sys[i]]->t;
+                int ti = p, tj = 0;
+                (void)ti; (void)tj;
+                double pairs = (double)s.tile * s.tile;
+                int nt = s.n_mob_tiles;
+                // recover (ti, tj) from the item order used by build_device
+                int q = p, a = 0;
+                int nft = (t.n_fix + s.tile - 1) / s.tile;
+                while (q >= (nt - a) + nft) { q -= (nt - a) + nft; ++a; }
+                int ni = std::min(s.tile, t.n_mob - a * s.tile);
+                if (q < nt - a) {
+                    int b2 = a + q;
+                    int nj = std::min(s.tile, t.n_mob - b2 * s.tile);
+                    pairs = b2 == a ? 0.5 * ni * (ni - 1) : (double)ni * nj;
+                } else {
+                    int f = q - (nt - a);
+                    pairs = (double)ni * std::min(s.tile, t.n_fix - f * s.tile);
+                }
+                items.push_back({pairs * pair_cost, make_int4(kItemReal, i, w, p)});
+            }
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
+    std::vector<int4> id(items.size());
+    for (size_t k = 0; k < items.size(); ++k) id[k] = items[k].d;
+
+    cudaError_t e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+    std::vector<void *> &o = m->dev;
+    auto chk = [&](cudaError_t x) { if (!e) e = x; };
+    SysDev *d_sys = nullptr;
+    BatchDev *d_bat = nullptr;
+    int *d_bs = nullptr, *d_wb = nullptr;
+    int4 *d_items = nullptr;
+    if (!e) chk(upload(o, &d_sys, sys.data(), sys.size()));
+    if (!e) chk(upload(o, &d_bat, bat.data(), bat.size()));
+    if (!e) chk(upload(o, &d_bs, bat_sys.data(), bat_sys.size()));
+    if (!e) chk(upload(o, &d_wb, wbase.data(), wbase.size()));
+    if (!e) chk(upload(o, &d_items, id.data(), id.size()));
+    MultiDev &md = m->m;
+    if (!e) chk(dalloc(o, &md.next, 1));
+    if (!e) chk(dalloc(o, &md.done, nw));
+    if (!e) chk(dalloc(o, &md.e_all, nw));
+    if (!e) chk(cudaMallocHost((void **)&m->pin, sizeof(double) * nw));
+    md.sys = d_sys;
+    md.bat = d_bat;
+    md.bat_sys = d_bs;
+    md.wbase = d_wb;
+    md.items = d_items;
+    md.n_items = (int)id.size();
+    md.n_walkers = nw;
+    m->smem = multi_energy_smem(sys, m->precision, &md.img_bytes);
+    if (!e) chk((cudaError_t)configure_multi(m->precision, m->smem, &m->grid));
+    if (!e) chk(cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming));
+    for (size_t k = 0; k < m->ctxs.size() && !e; ++k) {
+        cudaEvent_t ev;
+        chk(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        if (!e) m->ev_in.push_back(ev);
+    }
+    // capture the launch (counter resets + kernel) once; every call replays it
+    if (!e) {
+        cudaGraph_t g = nullptr;
+        chk(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+        if (!e) {
+            int le = launch_multi_energy(md, m->precision, m->grid, m->smem, m->stream);
+            cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
+            chk((cudaError_t)le);
+            chk(ce);
+        }
+        if (!e) chk(cudaGraphInstantiate(&m->exec, g, 0));
+        if (g) cudaGraphDestroy(g);
+    }
+    if (e) {
+        ewald_multi_destroy(m);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? EWALD_ERR_OOM : EWALD_ERR_CUDA;
+    }
+    *out = m;
+    return EWALD_OK;
+}
+
+void ewald_multi_destroy(ewald_multi *m) {
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    for (cudaEvent_t ev : m->ev_in) cudaEventDestroy(ev);
+    if (m->ev_out) cudaEventDestroy(m->ev_out);
+    free_all(m->dev);
+    if (m->pin) cudaFreeHost(m->pin);
+    if (m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+int ewald_multi_energy(ewald_multi *m, double *e_out, int on_device) {
+    if (!m || !e_out) return EWALD_ERR_ARG;
+    cudaError_t e = cudaSuccess;
+    // the batches' own streams first finish what they have queued
+    for (size_t k = 0; k < m->ctxs.size() && !e; ++k) {
+        e = cudaEventRecord(m->ev_in[k], m->ctxs[k]->stream);
+        if (!e) e = cudaStreamWaitEvent(m->stream, m->ev_in[k], 0);
+    }
+    if (!e) e = cudaGraphLaunch(m->exec, m->stream);
+    const size_t bytes = sizeof(double) * (size_t)m->m.n_walkers;
+    if (!e) e = cudaMemcpyAsync(on_device ? (void *)e_out : (void *)m->pin, m->m.e_all, bytes,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
+    if (!e) e = cudaEventRecord(m->ev_out, m->stream);
+    for (size_t k = 0; k < m->ctxs.size() && !e; ++k) e = cudaStreamWaitEvent(m->ctxs[k]->stream, m->ev_out, 0);
+    for (ewald_batch *b : m->batches) b->has_pending = false;
+    if (e) return cuda_fail(m->ctxs[0], e);
+    if (on_device) return EWALD_OK;
+    if ((e = cudaStreamSynchronize(m->stream))) return cuda_fail(m->ctxs[0], e);
+    std::memcpy(e_out, m->pin, bytes);
+    int st = EWALD_OK;
+    for (ewald_batch *b : m->batches) {
+        int s2 = sync_status(b);
+        if (s2 && !st) st = s2;
+    }
+    return st;
 }
 
 }  // extern "C"

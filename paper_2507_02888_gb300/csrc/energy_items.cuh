@@ -1,0 +1,232 @@
+// Work items of the full-energy path, as device functions shared by the
+// single-system kernels (energy_kernels.cu) and the persistent multi-system
+// kernel (multi_kernels.cu).
+//
+//   sfac_item : rho(G) of one walker over one chunk of G runs, and that
+//               chunk's reciprocal energy (paper Eq. (3) / Eq. (5) at z = 0,
+//               powers of e^{i b_k . r} buffered as in Eq. (10));
+//   real_item : real-space pair sum of one walker over one tile pair
+//               (Eq. (3), second term);
+//   combine_walker : E = E_real + E_madR + E_recip + E_self + E_bg (Eq. (2)).
+#pragma once
+#include "device_common.cuh"
+
+namespace ewald {
+
+__host__ __device__ inline size_t sfac_bytes(const SysDev &s, int precision, int te, int threads) {
+    size_t part = precision == EWALD_FP64 ? sizeof(Part<double>) : sizeof(Part<float>);
+    size_t cx = precision == EWALD_FP64 ? sizeof(Cx<double>) : sizeof(Cx<float>);
+    int W = (2 * s.n1max + 1) + (2 * s.n2max + 1) + (s.dim == 3 ? s.n3max + 1 : 0);
+    return align16(te * part) + align16((size_t)te * W * cx) + align16((threads / 32) * sizeof(double));
+}
+
+__host__ __device__ inline size_t real_work_bytes(const SysDev &s, int precision, int warps) {
+    size_t part = precision == EWALD_FP64 ? sizeof(Part<double>) : sizeof(Part<float>);
+    size_t qe = precision == EWALD_FP64 ? sizeof(QE<double>) : sizeof(QE<float>);
+    return 2 * align16(s.tile * part) + align16((size_t)warps * kQueueCap * qe) + align16(16 * sizeof(double));
+}
+
+// One CTA; blockDim.x threads, each owning one run of <= kRunLen consecutive
+// n1 in a row (n2, n3), walked away from the row's smallest |G|.  Electrons are staged in tiles of te; for each
+// electron of the tile the CTA buffers the powers e^{2 pi i n f_k},
+// n = -n_max..n_max, built by repeated multiplication from the base phase.
+// A thread starts its run from the product of three buffered powers and
+// steps along n1 by one complex multiplication per G.  Tile sums are in R
+// and are added into FP64.
+template <typename R, int DIM>
+__device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, int te, bool write_energy,
+                          unsigned char *smem) {
+    using C = Cx<R>;
+    const int W1 = 2 * s.n1max + 1, W2 = 2 * s.n2max + 1, W3 = DIM == 3 ? s.n3max + 1 : 0;
+    Part<R> *tp = (Part<R> *)smem;
+    C *P1 = (C *)(smem + align16(te * sizeof(Part<R>)));
+    C *P2 = P1 + (size_t)te * W1;
+    C *P3 = P2 + (size_t)te * W2;
+    double *red = (double *)(smem + align16(te * sizeof(Part<R>)) + align16((size_t)te * (W1 + W2 + W3) * sizeof(C)));
+
+    const int tid = threadIdx.x;
+    const int run = chunk * blockDim.x + tid;
+    const bool has = run < s.n_runs;
+    const int4 rn0 = has ? s.runs[run] : make_int4(0, 0, 0, 0);
+    const int dir = rn0.w < 0 ? -1 : 1;             // the run walks n1 = start + dir * r
+    const int4 rn = make_int4(rn0.x, rn0.y, rn0.z, rn0.w * dir);
+    double ax[kRunLen], ay[kRunLen];
+#pragma unroll
+    for (int r = 0; r < kRunLen; ++r) ax[r] = ay[r] = 0;
+
+    for (int e0 = 0; e0 < s.n_mob; e0 += te) {
+        const int ne = min(te, s.n_mob - e0);
+        __syncthreads();  // the previous tile's tables are no longer read
+        for (int t = tid; t < ne; t += blockDim.x) tp[t] = load_mobile<R>(s, b, w, e0 + t, DIM);
+        __syncthreads();
+        for (int t = tid; t < ne * DIM; t += blockDim.x) {
+            const int e = t / DIM, k = t - e * DIM;
+            R sn, cs;
+            FP<R>::sincospi2(FP<R>::frac(tp[e].u[k]), &sn, &cs);
+            const C base = {cs, sn};
+            C p = {R(1), R(0)};
+            if (k < 2) {
+                const int nm = k == 0 ? s.n1max : s.n2max;
+                C *P = k == 0 ? P1 + (size_t)e * W1 : P2 + (size_t)e * W2;
+                P[nm] = p;
+                for (int n = 1; n <= nm; ++n) {
+                    p = cmul(p, base);
+                    P[nm + n] = p;
+                    P[nm - n] = {p.x, -p.y};
+                }
+            } else {
+                C *P = P3 + (size_t)e * W3;
+                P[0] = p;
+                for (int n = 1; n < W3; ++n) {
+                    p = cmul(p, base);
+                    P[n] = p;
+                }
+            }
+        }
+        __syncthreads();
+        R tx[kRunLen], ty[kRunLen];
+#pragma unroll
+        for (int r = 0; r < kRunLen; ++r) tx[r] = ty[r] = 0;
+        if (has) {
+            for (int e = 0; e < ne; ++e) {
+                const R q = tp[e].q;
+                C z = cmul(P1[(size_t)e * W1 + rn.x + s.n1max], P2[(size_t)e * W2 + rn.y + s.n2max]);
+                if (DIM == 3) z = cmul(z, P3[(size_t)e * W3 + rn.z]);
+                const C step = P1[(size_t)e * W1 + s.n1max + dir];
+#pragma unroll
+                for (int r = 0; r < kRunLen; ++r) {
+                    if (r < rn.w) {
+                        tx[r] += q * z.x;
+                        ty[r] += q * z.y;
+                        z = cmul(z, step);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRunLen; ++r) {
+            ax[r] += (double)tx[r];
+            ay[r] += (double)ty[r];
+        }
+    }
+
+    const int slots = s.n_runs * s.run_len;
+    double epart = 0;
+    if (has) {
+        double2 *rho = b.rho + (size_t)w * slots;
+#pragma unroll
+        for (int r = 0; r < kRunLen; ++r) {
+            if (r < s.run_len) {
+                const int slot = r * s.n_runs + run;
+                double2 v = make_double2(0.0, 0.0);
+                if (r < rn.w) {
+                    v.x = ax[r];
+                    v.y = ay[r];
+                    if (s.rho_fix) {
+                        v.x += s.rho_fix[slot].x;
+                        v.y += s.rho_fix[slot].y;
+                    }
+                    epart += s.gw_d[slot] * (v.x * v.x + v.y * v.y);
+                }
+                rho[slot] = v;
+            }
+        }
+    }
+    if (write_energy) {
+        double tot = block_sum(epart, red);
+        if (tid == 0) b.part_recip[(size_t)w * s.n_gchunks + chunk] = tot;
+    }
+}
+
+// One CTA, any number of warps.  The tile pair's particles are staged in
+// shared memory; each warp takes 32 x 32 sub-tiles (lane = i, loop over j),
+// diagonal tiles only their upper triangle.  Images inside the cutoff go
+// through the warp queue.  Every sub-tile is summed on its own and the
+// sub-tile sums are added in sub-tile order in FP64, so the item's partial
+// sum does not depend on how many warps the CTA has.
+// ims must already hold this system's images; work is this item's scratch.
+template <typename R, int DIM>
+__device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, const ImageSmem<R> &ims,
+                          unsigned char *work) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    size_t off = 0;
+    Part<R> *ti = (Part<R> *)(work + off);
+    off += align16(s.tile * sizeof(Part<R>));
+    Part<R> *tj = (Part<R> *)(work + off);
+    off += align16(s.tile * sizeof(Part<R>));
+    QE<R> *qbase = (QE<R> *)(work + off);
+    off += align16((size_t)nw * kQueueCap * sizeof(QE<R>));
+    double *red = (double *)(work + off);
+
+    const int S = s.tile / 32;
+    const int2 tt = s.items[p];
+    const bool fixedj = tt.y >= s.n_mob_tiles;
+    const int i0 = tt.x * s.tile;
+    const int j0 = (fixedj ? tt.y - s.n_mob_tiles : tt.y) * s.tile;
+    const int nj = fixedj ? s.n_fix : s.n_mob;
+    __syncthreads();  // the previous item's tiles are no longer read
+    for (int t = tid; t < s.tile; t += blockDim.x) {
+        ti[t] = load_mobile<R>(s, b, w, i0 + t, DIM);
+        tj[t] = fixedj ? load_fixed<R>(s, j0 + t, DIM) : load_mobile<R>(s, b, w, j0 + t, DIM);
+    }
+    __syncthreads();
+    WarpQueue<R> wq{qbase + warp * kQueueCap, 0, FP<R>::coin2(s), b.status};
+    const typename FP<R>::K tk = FP<R>::term_consts(s);
+    const bool diag = !fixedj && tt.x == tt.y;
+    const int nst = diag ? S * (S + 1) / 2 : S * S;
+    for (int st = warp; st < nst; st += nw) {
+        int a, c;
+        if (diag) {
+            a = 0;
+            int rem = st;
+            while (rem >= S - a) {
+                rem -= S - a;
+                ++a;
+            }
+            c = a + rem;
+        } else {
+            a = st / S;
+            c = st - a * S;
+        }
+        const Part<R> pi = ti[a * 32 + lane];
+        const bool vi = i0 + a * 32 + lane < s.n_mob;
+        Acc<R> acc;
+        for (int jj = 0; jj < 32; ++jj) {
+            const int lj = c * 32 + jj;
+            const bool v = vi && (j0 + lj < nj) && (!(diag && a == c) || lane < jj);
+            pair_images<R, DIM>(s, pi, tj[lj], v, R(1), ims.img, ims.cand, wq, acc, lane);
+        }
+        wq.drain(acc, tk, lane);
+        const double v = warp_sum(acc.get());
+        if (lane == 0) red[st] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0;
+        for (int k = 0; k < nst; ++k) t += red[k];
+        b.part_real[(size_t)w * s.n_items + p] = t;
+    }
+}
+
+// E = E_real + E_madR + E_recip + E_self + E_bg for walker w; partial sums
+// are added in a fixed order, so the result does not depend on scheduling.
+__device__ inline double combine_walker(const SysDev &s, const BatchDev &b, int w) {
+    double er = 0;
+    for (int p = 0; p < s.n_items; ++p) er += b.part_real[(size_t)w * s.n_items + p];
+    er += s.e_II;
+    double ek = 0;
+    for (int c = 0; c < s.n_gchunks; ++c) ek += b.part_recip[(size_t)w * s.n_gchunks + c];
+    double *cp = b.comp + (size_t)w * 5;
+    cp[0] = er;
+    cp[1] = s.e_madR;
+    cp[2] = ek;
+    cp[3] = s.e_self;
+    cp[4] = s.e_bg;
+    const double e = er + s.e_madR + ek + s.e_self + s.e_bg;
+    b.e[w] = e;
+    b.acc_count[w] = 0;
+    b.pend_k[w] = -1;
+    return e;
+}
+
+}  // namespace ewald

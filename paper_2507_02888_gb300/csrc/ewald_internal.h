@@ -3,7 +3,8 @@
 // Data layout in device memory (per context = one periodic system):
 //   images   : candidate lattice vectors R (Cartesian), FP64 and FP32 copies
 //   cand     : per displacement cell, indices into images (uint16), padded
-//   runs     : G rows split into runs of <= run_len consecutive n1 (int4)
+//   runs     : G rows split into runs of <= run_len consecutive n1 walked away
+//              from the row's smallest |G| (int4: n1 start, n2, n3, dir * len)
 //   gw       : weight of every G slot, 2 C f(G) (0 for padding slots)
 //   rho_fix  : fixed particles' rho(G) per slot
 // and per walker batch:
@@ -40,14 +41,15 @@ enum : int { ST_COINCIDENT = 1, ST_BAD_INDEX = 2, ST_NONFINITE = 4, ST_TIMEOUT =
 struct SysDev {
     int dim, n_mob, n_fix, mob_stride, fix_stride;
     double A64[3][3];   // A[k][x] * 2^-64: Cartesian x of a uint64 fractional difference
-    float A32[3][3];    // A[k][x] * 2^-32 for the FP32 path
+    float A32[3][3];    // A[k][x] * 2^-32 for the FP32 path (rounded) ...
+    float A32lo[3][3];  // ... and its rounding residual: A * 2^-32 = A32 + A32lo
     double A[3][3];     // lattice rows a_k
     double Binv[3][3];  // f_k = sum_x Binv[k][x] r_x (fractional coordinates)
     double alpha, rc2, coin2;
     float alpha_f, rc2_f, coin2_f;
     float alpha_lo_f, alpha2_f, alpha2_lo_f;  // alpha = alpha_f + alpha_lo_f, alpha^2 likewise
     // real space
-    int n_img, sub_bits, cand_max;
+    int n_img, sub_bits, cand_max;  // images [n_img + 1]: the last is a far sentinel
     const Img64 *img_d;
     const float4 *img_f;
     const unsigned short *cand;
@@ -55,9 +57,9 @@ struct SysDev {
     int tile, n_mob_tiles, n_items;  // pair tiles (T = tile) and items per walker
     const int2 *items;               // (ti, tj); tj >= n_mob_tiles -> fixed tile tj - n_mob_tiles
     // reciprocal space
-    int n_runs, run_len, n_gh, n_gchunks;
+    int n_runs, run_len, n_gh, n_gchunks, sfac_te;
     int n1max, n2max, n3max;
-    const int4 *runs;  // (n1 start, n2, n3, length)
+    const int4 *runs;  // (n1 start, n2, n3, dir * length), dir = +-1
     const double *gw_d;
     const float *gw_f;
     const double2 *rho_fix;  // may be null
@@ -119,7 +121,7 @@ struct LaunchCfg {
     size_t real_smem, sfac_smem, move_smem;
     int sfac_te;        // electrons per structure-factor tile
 };
-int configure_launch(const SysDev &s, int precision, LaunchCfg *cfg);
+int configure_launch(SysDev &s, int precision, LaunchCfg *cfg);
 int launch_ingest(const SysDev &s, const BatchDev &b, const double *pos, cudaStream_t st);
 int launch_positions_out(const SysDev &s, const BatchDev &b, double *pos, cudaStream_t st);
 int launch_real(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg,

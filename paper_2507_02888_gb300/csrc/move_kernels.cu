@@ -49,14 +49,15 @@ template <typename R, int DIM, typename F>
 __device__ inline void for_each_delta(const SysDev &s, const MoveTables<R> &t, R qk, F &&f) {
     for (int run = threadIdx.x; run < s.n_runs; run += blockDim.x) {
         const int4 rn = s.runs[run];
+        const int dir = rn.w < 0 ? -1 : 1, len = rn.w * dir;
         Cx<R> zo = cmul(t.P[0][0][rn.x + s.n1max], t.P[0][1][rn.y + s.n2max]);
         Cx<R> zn = cmul(t.P[1][0][rn.x + s.n1max], t.P[1][1][rn.y + s.n2max]);
         if (DIM == 3) {
             zo = cmul(zo, t.P[0][2][rn.z]);
             zn = cmul(zn, t.P[1][2][rn.z]);
         }
-        const Cx<R> so = t.P[0][0][s.n1max + 1], sn = t.P[1][0][s.n1max + 1];
-        for (int r = 0; r < rn.w; ++r) {
+        const Cx<R> so = t.P[0][0][s.n1max + dir], sn = t.P[1][0][s.n1max + dir];
+        for (int r = 0; r < len; ++r) {
             const Cx<R> d = {qk * (zn.x - zo.x), qk * (zn.y - zo.y)};
             f(r * s.n_runs + run, d);
             zo = cmul(zo, so);
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kMoveThreads)
     __syncthreads();
 
     // real space: slots (other particle j, old/new), j over mobile != k then fixed
-    WarpQueue<R> wq{m.queues + warp * kQueueCap, 0};
+    WarpQueue<R> wq{m.queues + warp * kQueueCap, 0, FP<R>::coin2(s), b.status};
     Acc<R> acc;
     const int n_other = s.n_mob - 1 + s.n_fix;
     const int total = 2 * n_other;
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kMoveThreads)
         else if (jj < s.n_mob - 1) pj = load_mobile<R>(s, b, w, jj < k ? jj : jj + 1, DIM);
         else pj = load_fixed<R>(s, jj - (s.n_mob - 1), DIM);
         pair_images<R, DIM>(s, which ? pnew : pold, pj, v, which ? R(1) : R(-1), m.ims.img, m.ims.cand,
-                            m.ims.cand_len, wq, acc, lane, b.status);
+                            wq, acc, lane);
     }
     wq.drain(acc, FP<R>::term_consts(s), lane);
     double tot = acc.get();

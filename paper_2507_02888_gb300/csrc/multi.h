@@ -1,0 +1,29 @@
+// Device-side description of a multi-system launch (multi_kernels.cu).
+#pragma once
+#include <vector>
+
+#include "ewald_internal.h"
+
+namespace ewald {
+
+constexpr int kMultiThreads = 256;
+enum : int { kItemSfac = 0, kItemReal = 1 };
+
+struct MultiDev {
+    const SysDev *sys;     // [n_sys]
+    const BatchDev *bat;   // [n_bat]
+    const int *bat_sys;    // [n_bat] system of each batch
+    const int *wbase;      // [n_bat] first walker of each batch in the concatenation
+    const int4 *items;     // [n_items] (kind, batch, walker, sub), longest first
+    int n_items, n_walkers;
+    size_t img_bytes;      // shared memory reserved for the image table
+    int *next;             // work counter
+    int *done;             // [n_walkers] items completed per walker
+    double *e_all;         // [n_walkers] energies
+};
+
+size_t multi_energy_smem(const std::vector<SysDev> &sys, int precision, size_t *img_bytes);
+int configure_multi(int precision, size_t smem, int *grid);
+int launch_multi_energy(const MultiDev &m, int precision, int grid, size_t smem, cudaStream_t st);
+
+}  // namespace ewald

@@ -172,7 +172,8 @@ static int build_cand(const HostTables &t, int bits, std::vector<unsigned short>
         longest = std::max(longest, (int)lists[s].size());
     }
     if (cand) {
-        cand->assign((size_t)n_sub * std::max(longest, 1), 0);
+        // pad every list to the longest with the sentinel image n_img (far away)
+        cand->assign((size_t)n_sub * std::max(longest, 1), (unsigned short)n_img);
         len->assign(n_sub, 0);
         for (int s = 0; s < n_sub; ++s) {
             (*len)[s] = (int)lists[s].size();
@@ -225,18 +226,35 @@ static void build_gvectors(HostTables *t) {
             }
             if (lo <= hi) rows.push_back({n2, n3, lo, hi});
         }
-    // split rows into runs of <= run_len consecutive n1, lengths as equal as possible
+    // Split every row at its smallest |G| and walk outward in both directions,
+    // in runs of <= run_len consecutive n1 (lengths as equal as possible).  A
+    // run is (n1 start, n2, n3, dir * length), dir = +1 or -1.  The FP32
+    // recurrence error grows along a run; starting each run at the small-|G|
+    // end keeps it smallest where the weights f(G) are largest.
     t->runs.clear();
     t->gn.clear();
     t->n1max = t->n2max = t->n3max = 0;
-    for (auto &r : rows) {
-        int L = r.hi - r.lo + 1, nr = (L + t->run_len - 1) / t->run_len;
-        int start = r.lo;
+    auto split = [&](int start, int L, int dir, int n2, int n3) {
+        if (L <= 0) return;
+        int nr = (L + t->run_len - 1) / t->run_len;
         for (int j = 0; j < nr; ++j) {
             int len = L / nr + (j < L % nr ? 1 : 0);
-            t->runs.insert(t->runs.end(), {start, r.n2, r.n3, len});
-            start += len;
+            t->runs.insert(t->runs.end(), {start, n2, n3, dir * len});
+            start += dir * len;
         }
+    };
+    for (auto &r : rows) {
+        int mid = r.lo;
+        double best = 1e300;
+        for (int n1 = r.lo; n1 <= r.hi; ++n1) {
+            double G[3] = {0, 0, 0};
+            for (int y = 0; y < dim; ++y)
+                G[y] = n1 * t->B[0][y] + r.n2 * t->B[1][y] + (dim == 3 ? r.n3 * t->B[2][y] : 0);
+            double g = norm_n(G, dim);
+            if (g < best) { best = g; mid = n1; }
+        }
+        split(mid, r.hi - mid + 1, +1, r.n2, r.n3);
+        split(mid - 1, mid - r.lo, -1, r.n2, r.n3);
         t->n1max = std::max(t->n1max, std::max(std::abs(r.lo), std::abs(r.hi)));
         t->n2max = std::max(t->n2max, std::abs(r.n2));
         t->n3max = std::max(t->n3max, std::abs(r.n3));
@@ -248,8 +266,9 @@ static void build_gvectors(HostTables *t) {
     double C = dim == 3 ? 2 * kPi / t->volume : kPi / t->volume;
     for (int run = 0; run < n_runs; ++run) {
         const int *rn = &t->runs[4 * run];
-        for (int j = 0; j < rn[3]; ++j) {
-            int n[3] = {rn[0] + j, rn[1], rn[2]};
+        const int dir = rn[3] > 0 ? 1 : -1, len = std::abs(rn[3]);
+        for (int j = 0; j < len; ++j) {
+            int n[3] = {rn[0] + dir * j, rn[1], rn[2]};
             double G[3] = {0, 0, 0};
             for (int y = 0; y < dim; ++y)
                 for (int k = 0; k < dim; ++k) G[y] += n[k] * t->B[k][y];
@@ -307,8 +326,9 @@ static void build_constants(HostTables *t) {
     for (int I = 0; I < t->n_fix; ++I) cart_to_frac(*t, &t->fix_pos[I * dim], &fr[3 * I]);
     for (int run = 0; run < n_runs; ++run) {
         const int *rn = &t->runs[4 * run];
-        for (int j = 0; j < rn[3]; ++j) {
-            int n[3] = {rn[0] + j, rn[1], rn[2]};
+        const int dir = rn[3] > 0 ? 1 : -1, len = std::abs(rn[3]);
+        for (int j = 0; j < len; ++j) {
+            int n[3] = {rn[0] + dir * j, rn[1], rn[2]};
             double re = 0, im = 0;
             for (int I = 0; I < t->n_fix; ++I) {
                 double ph = 0;

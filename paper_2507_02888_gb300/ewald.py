@@ -51,11 +51,14 @@ class Info(ctypes.Structure):
 _lib = None
 _live_batches = weakref.WeakSet()
 _live_contexts = weakref.WeakSet()
+_live_multis = weakref.WeakSet()
 
 
 @atexit.register
 def _close_all():
     """Free library objects while the CUDA runtime is still up (interpreter exit)."""
+    for m in list(_live_multis):
+        m.close()
     for b in list(_live_batches):
         b.close()
     for c in list(_live_contexts):
@@ -80,6 +83,9 @@ SIGNATURES = [
     ("ewald_accept_move", _c_int, [_vp, _vp, _c_int]),
     ("ewald_resum", _c_int, [_vp]),
     ("ewald_batch_get_rho", _c_int, [_vp, _vp, _c_int]),
+    ("ewald_multi_create", _c_int, [_vp, _c_int, ctypes.POINTER(_vp)]),
+    ("ewald_multi_energy", _c_int, [_vp, _vp, _c_int]),
+    ("ewald_multi_destroy", None, [_vp]),
     ("ewald_set_timing", _c_int, [_vp, _c_int]),
     ("ewald_get_timing", _c_int, [_vp, _vp, _vp]),
 ]
@@ -282,6 +288,38 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             _lib.ewald_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """Batches of different systems evaluated by one persistent launch (graph-replayed)."""
+
+    def __init__(self, batches):
+        self.batches = list(batches)
+        arr = (_vp * len(self.batches))(*[b._h for b in self.batches])
+        h = _vp()
+        _check(_lib.ewald_multi_create(arr, len(self.batches), ctypes.byref(h)))
+        self._h = h
+        self.W = sum(b.W for b in self.batches)
+        _live_multis.add(self)
+
+    def energy(self, out=None):
+        """Energies of every walker, batches concatenated in order."""
+        if out is None:
+            out = np.zeros(self.W)
+        p, dev = _ptr(out)
+        _check(_lib.ewald_multi_energy(self._h, p, dev))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ewald_multi_destroy(self._h)
             self._h = None
 
     def __del__(self):
