@@ -53,6 +53,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=2000)
+    p.add_argument("--serve-requests-fp64", type=int, default=120)
     return p.parse_args()
 
 
@@ -341,10 +345,96 @@ def run_ours(args, rank, world, local_rank):
         b.close()
         ctx.close()
 
+    # ---- batched form (uneven systems in one persistent launch) and serving form
+    if not args.no_batched:
+        result["batched"] = run_batched(stream, 5)
+    if not args.no_serving:
+        sv = run_serving(stream, "mixed", args.serve_requests)
+        sv["fp64"] = run_serving(stream, "fp64", args.serve_requests_fp64)
+        result["serving"] = sv
+
     # ---- CPU oracle on the host cores (rank 0 only)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_oracle_rate(w, info["r_cutoff"], info["g_cutoff"], args.cpu_seconds)
     return result
+
+
+def run_batched(stream, steps):
+    """Batched form: diamond (864 e + 216 ions, 1024 walkers) and 2D hex (338 e,
+    2048 walkers) in one persistent launch per energy call, tilings autotuned."""
+    import torch
+    from paper_2507_02888_gb300 import ewald, inputs
+    ws = [inputs.workload("diamond_3x3x3"), inputs.workload("heg2d_hex_n338")]
+    ctxs = [ewald.context_for(w, precision="mixed", stream=stream) for w in ws]
+    bs = []
+    tune = []
+    for c, w in zip(ctxs, ws):
+        b = ewald.Batch(c, w["n_walkers"])
+        b.set_positions(w["pos"])
+        tune.append(b.autotune())
+        bs.append(b)
+    m = ewald.Multi(bs)
+    Wt = sum(b.W for b in bs)
+    out = torch.empty(Wt, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            m.energy(out)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(steps):
+            m.energy(out)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t_multi = ev[0].elapsed_time(ev[1])
+        # the same walkers, one energy launch sequence per batch
+        ev[0].record(stream)
+        for _ in range(steps):
+            for b in bs:
+                b.energy(out[:b.W])
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t_sep = ev[0].elapsed_time(ev[1])
+    m.close()
+    return {"value": Wt * steps / (t_multi / 1e3), "unit": "walker energies/s",
+            "workload": "diamond_3x3x3 (W=1024) + heg2d_hex_n338 (W=2048), one persistent launch",
+            "separate_batches": Wt * steps / (t_sep / 1e3), "steps": steps,
+            "tiling": [{"pair_tile": t["pair_tile"], "subcell_bits": t["subcell_bits"]} for t in tune]}
+
+
+SERVE_SYSTEMS = ["heg3d_sc_n54", "heg3d_sc_n128", "heg2d_hex_n338", "heg3d_sc_n512", "heg3d_fcc_n1024",
+                 "diamond_3x3x3"]
+
+
+def run_serving(stream, precision, n_requests, seed=4242):
+    """Serving form: Poisson stream of requests over the six systems of the mix,
+    W ~ U{1..512} walkers, M ~ U{1..200} moves, rate 0.8 x the saturated rate."""
+    from paper_2507_02888_gb300 import ewald, inputs, serve
+    rng = np.random.default_rng(seed)
+    ws = {}
+    for name in SERVE_SYSTEMS:
+        w = inputs.workload(name, 512)
+        ws[name] = (ewald.context_for(w, precision=precision, stream=stream), w["pos"], w["sigma"])
+
+    def make(n, rate):
+        reqs, t = [], 0.0
+        for i in range(n):
+            name = SERVE_SYSTEMS[rng.integers(len(SERVE_SYSTEMS))]
+            ctx, pos, sigma = ws[name]
+            W, M = int(rng.integers(1, 513)), int(rng.integers(1, 201))
+            t = 0.0 if rate is None else t + rng.exponential(1.0 / rate)
+            reqs.append((t, ctx, pos[:W], M, sigma, int(rng.integers(1, 2 ** 62))))
+        return reqs
+
+    srv = serve.Server(precision, max_walkers=16384)
+    sat = serve.run_stream(srv, make(max(20, n_requests // 8), None))
+    sat_rate = len(sat["results"]) / sat["elapsed_s"]
+    lam = 0.8 * sat_rate
+    res = serve.run_stream(srv, make(n_requests, lam))
+    srv.close()
+    return {"moves_per_s": res["moves"] / res["elapsed_s"], "unit": "walker moves/s (propose+accept)",
+            "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"], "requests": n_requests,
+            "arrival_rate_per_s": lam, "saturated_moves_per_s": sat["moves"] / sat["elapsed_s"],
+            "saturated_requests_per_s": sat_rate, "elapsed_s": res["elapsed_s"]}
 
 
 def run_reference(args, rank, world):

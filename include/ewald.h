@@ -82,6 +82,7 @@ typedef struct {
     int n_g_half;         /* G vectors kept, one of each +-G pair */
     int n_images;         /* distinct lattice vectors that may meet the real-space cutoff */
     int subcell_bits;     /* real-space displacement cells: 2^bits per axis */
+    int pair_tile;        /* particles per side of a real-space pair tile (32, 64, 128) */
     int max_candidates;   /* longest candidate-image list of a displacement cell */
     int n_runs, run_len;  /* G rows split into runs of <= run_len consecutive n1 */
     double e_madelung;    /* 1/2 sum q^2 sum_{R!=0} erfc(alpha R)/R  (all charges) */
@@ -106,6 +107,10 @@ int ewald_get_gvectors(const ewald_ctx *ctx, int *nvec);
  * that checks it). */
 int ewald_last_error(const ewald_ctx *ctx);
 const char *ewald_strerror(int code);
+/* A one-line description of the context's last failure (argument checked,
+ * CUDA call and its error string, ...); valid until the next call on the
+ * context.  Never NULL. */
+const char *ewald_last_error_message(const ewald_ctx *ctx);
 
 /* Walker batches.  A batch owns the walkers' positions (fixed-point
  * fractional coordinates), their rho(G) and the pending moves.  Before the
@@ -149,8 +154,9 @@ int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device);
  * persistent kernel launch per call.  The work items (walker x chunk of G
  * runs, walker x pair tile) are ordered longest first at creation and taken
  * by the CTAs from an atomic counter; the CTA that finishes a walker's last
- * item adds up its energy in a fixed order, so every result equals the
- * single-batch ewald_energy of that walker bit for bit.  The launch is
+ * item adds up its energy in a fixed order, so a result does not depend on
+ * the schedule or the other batches and equals the single-batch
+ * ewald_energy of that walker to rounding.  The launch is
  * captured once in a CUDA graph and replayed by every call.  The batches
  * must keep their positions set and outlive the multi object; their
  * contexts' streams are ordered with the multi's own stream by events.
@@ -163,6 +169,60 @@ int ewald_multi_create(ewald_batch *const *batches, int n_batches, ewald_multi *
  * Also rebuilds every walker's rho(G), like ewald_energy. */
 int ewald_multi_energy(ewald_multi *m, double *e_out, int on_device);
 void ewald_multi_destroy(ewald_multi *m);
+
+/* Serving form: continuous batching of walker batches from concurrent runs.
+ * A request is W walkers of one system (a context of the server's
+ * precision) that each make n_steps single-particle moves: particle k
+ * uniform, Gaussian displacement of standard deviation sigma per axis,
+ * accepted with probability accept_prob (there is no wave function here),
+ * all drawn on the device from a counter-based SplitMix64 stream of the
+ * request's seed.  Requests queue on submission and are admitted between
+ * steps while the server's walker slots and device-memory budget allow;
+ * from admission on their rho(G) stays on the device.  Every step advances
+ * every active request by one move in one persistent launch (replayed from
+ * a CUDA graph), whatever the mix of systems; finished requests are retired
+ * between steps.  A walker's result is the same alone and in any mix.
+ * Results: the final energy of every walker (initial Ewald energy plus the
+ * accepted energy changes) and its number of accepted moves.  The contexts
+ * must outlive the server.  (Paper Sec. 2.1: VMC and DMC are sequences of
+ * single-particle moves; Sec. 2.2: the Ewald data stay on the device.)
+ * hbm_budget_bytes <= 0 takes 80% of the free device memory. */
+typedef struct ewald_server ewald_server;
+int ewald_server_create(int precision, int max_walkers, double hbm_budget_bytes, void *cuda_stream,
+                        ewald_server **out);
+void ewald_server_destroy(ewald_server *srv);
+/* pos: host [n_walkers][N][dim], copied.  *request_id receives the id. */
+int ewald_server_submit(ewald_server *srv, ewald_ctx *system, const double *pos, int n_walkers,
+                        int n_steps, double sigma, double accept_prob, unsigned long long seed,
+                        int *request_id);
+/* Retire finished requests, admit queued ones, and queue one move of every
+ * active request; returns without waiting for the device. */
+int ewald_server_step(ewald_server *srv, int *n_active, int *n_queued);
+/* EWALD_OK and the results (host arrays [W], either may be NULL) once the
+ * request is done, EWALD_ERR_STATE before; latency_ms = submission to
+ * completion as seen by the host. */
+int ewald_server_result(ewald_server *srv, int request_id, double *energies, int *n_accepted,
+                        double *latency_ms);
+/* Wait until everything queued on the server's stream has run. */
+int ewald_server_drain(ewald_server *srv);
+const char *ewald_server_error_message(const ewald_server *srv);
+
+/* Autotuner.  Times the real-space kernel on (up to 512 of) the batch's
+ * walkers for every allowed real-space tiling - pair tiles of 32, 64 or 128
+ * particles per side x 2^bits displacement cells per axis (candidate lists
+ * <= 48 KB) - and keeps the fastest in the batch's context.  With
+ * cache_path (may be NULL) the result is looked up first and stored after
+ * tuning in a small JSON file keyed by the system's shape and the GPU name;
+ * ewald_create also applies a cached tiling when the environment variable
+ * EWALD_TUNE_CACHE names such a file.  Retune before creating multi objects
+ * that include the context: a multi keeps the tiling it was created with. */
+typedef struct {
+    int pair_tile, subcell_bits;
+    double ms;       /* real-space kernel time of the chosen tiling, ms */
+    int n_tried;     /* tilings timed (0 if taken from the cache) */
+    int from_cache;
+} ewald_tune_result;
+int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *res);
 
 /* Kernel timers of a context (in the spirit of the paper's per-subroutine
  * timers, Sec. 3.2).  When enabled, every kernel the context launches is

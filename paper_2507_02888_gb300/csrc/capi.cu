@@ -4,89 +4,68 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
 #include <new>
 #include <utility>
 #include <string>
 #include <vector>
 
-#include "device_common.cuh"
+#include "capi_internal.h"
 #include "multi.h"
 
 using namespace ewald;
 
-struct ewald_ctx {
-    HostTables t;
-    SysDev s{};
-    LaunchCfg cfg{};
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::vector<void *> dev;
-    int *d_g2slot = nullptr;
-    int n_batches = 0;        // live batches; the context outlives them
-    bool destroy_pending = false;
-    int last_error = EWALD_OK;
-    std::string why;
-    // kernel timers
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
-    double t_ms[KT_COUNT] = {};
-    long long t_n[KT_COUNT] = {};
-};
-
-struct ewald_batch {
-    ewald_ctx *ctx = nullptr;
-    BatchDev b{};
-    std::vector<void *> dev;
-    bool has_pos = false, has_pending = false;
-    bool counted = false;  // included in ctx->n_batches
-    // host-I/O staging: pinned host buffer and device scratch for host inputs
-    void *pin = nullptr;
-    size_t pin_bytes = 0;
-    double *d_io = nullptr;   // [W][N][dim] doubles (positions, rho, components)
-    size_t d_io_bytes = 0;
-    int *d_k = nullptr;
-    double *d_rnew = nullptr, *d_de = nullptr;
-    unsigned char *d_acc = nullptr;
-};
-
 namespace {
 
-int fail(ewald_ctx *c, int code, const char *why = nullptr) {
-    if (c && code) {
-        c->last_error = code;
-        if (why) c->why = why;
-    }
-    return code;
-}
-
-int cuda_fail(ewald_ctx *c, cudaError_t e) {
-    if (c) c->why = cudaGetErrorString(e);
-    return fail(c, EWALD_ERR_CUDA);
-}
-
-template <typename T>
-cudaError_t dalloc(std::vector<void *> &owned, T **p, size_t count) {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-    if (e == cudaSuccess) owned.push_back(*p);
-    return e;
-}
-
-template <typename T>
-cudaError_t upload(std::vector<void *> &owned, T **p, const T *src, size_t count) {
-    cudaError_t e = dalloc(owned, p, count);
-    if (e) return e;
-    if (count) e = cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice);
-    return e;
-}
+using namespace ewald_capi;
 
 unsigned long long to_fixed(double f) {
     f -= std::floor(f);
     if (f >= 1.0) f = 0.0;
     return (unsigned long long)std::ldexp(f, 64);
+}
+
+void free_one(std::vector<void *> &v, const void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i] == p) {
+            cudaFree(v[i]);
+            v.erase(v.begin() + i);
+            return;
+        }
+}
+
+// Real-space tiling of a context: pair tiles of 32 x S particles per side
+// and 2^bits displacement cells per axis; rebuilds the candidate lists and
+// the item table on the device and the launch configuration.
+int apply_tiling(ewald_ctx *c, int S, int bits) {
+    HostTables &t = c->t;
+    SysDev &s = c->s;
+    cudaError_t e;
+    if (bits != t.sub_bits || t.cand.empty()) set_subcells(&t, bits);
+    free_one(c->dev, s.cand);
+    free_one(c->dev, s.items);
+    s.cand = nullptr;
+    s.items = nullptr;
+    s.sub_bits = t.sub_bits;
+    s.cand_max = t.cand_max;
+    if ((e = upload(c->dev, (unsigned short **)&s.cand, t.cand.data(), t.cand.size()))) return cuda_fail(c, e);
+    s.tile = 32 * S;
+    s.n_mob_tiles = (t.n_mob + s.tile - 1) / s.tile;
+    int nft = (t.n_fix + s.tile - 1) / s.tile;
+    std::vector<int2> items;
+    for (int i = 0; i < s.n_mob_tiles; ++i) {
+        for (int j = i; j < s.n_mob_tiles; ++j) items.push_back(make_int2(i, j));
+        for (int f = 0; f < nft; ++f) items.push_back(make_int2(i, s.n_mob_tiles + f));
+    }
+    s.n_items = (int)items.size();
+    if ((e = upload(c->dev, (int2 **)&s.items, items.data(), items.size()))) return cuda_fail(c, e);
+    if ((e = (cudaError_t)configure_launch(s, t.precision, &c->cfg))) return cuda_fail(c, e);
+    return EWALD_OK;
 }
 
 int build_device(ewald_ctx *c) {
@@ -117,6 +96,9 @@ int build_device(ewald_ctx *c) {
     double L = std::pow(t.volume, 1.0 / dim);
     s.coin2 = 1e-20 * L * L;
     s.coin2_f = (float)s.coin2;
+    // close radius: 0.3 of the mean spacing of all charges
+    const double spacing = std::pow(t.volume / (double)(t.n_mob + t.n_fix), 1.0 / dim);
+    s.close2_f = (float)(0.09 * spacing * spacing);
     cudaError_t e;
     // images
     int n_img = (int)t.img.size() / 3;
@@ -130,28 +112,8 @@ int build_device(ewald_ctx *c) {
     imd[n_img] = Img64{1e18, 1e18, 1e18, 0.0};
     imf[n_img] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
     s.n_img = n_img;
-    s.sub_bits = t.sub_bits;
-    s.cand_max = t.cand_max;
     if ((e = upload(o, (Img64 **)&s.img_d, imd.data(), imd.size()))) return cuda_fail(c, e);
     if ((e = upload(o, (float4 **)&s.img_f, imf.data(), imf.size()))) return cuda_fail(c, e);
-    if ((e = upload(o, (unsigned short **)&s.cand, t.cand.data(), t.cand.size()))) return cuda_fail(c, e);
-    if ((e = upload(o, (int **)&s.cand_len, t.cand_len.data(), t.cand_len.size()))) return cuda_fail(c, e);
-    // pair tiles: 32 x S particles per side
-    int S = t.n_mob >= 128 ? 4 : (t.n_mob >= 64 ? 2 : 1);
-    if (const char *env = std::getenv("EWALD_TILE_SUBTILES")) {
-        int v = std::atoi(env);
-        if (v == 1 || v == 2 || v == 4) S = v;
-    }
-    s.tile = 32 * S;
-    s.n_mob_tiles = (t.n_mob + s.tile - 1) / s.tile;
-    int nft = (t.n_fix + s.tile - 1) / s.tile;
-    std::vector<int2> items;
-    for (int i = 0; i < s.n_mob_tiles; ++i) {
-        for (int j = i; j < s.n_mob_tiles; ++j) items.push_back(make_int2(i, j));
-        for (int f = 0; f < nft; ++f) items.push_back(make_int2(i, s.n_mob_tiles + f));
-    }
-    s.n_items = (int)items.size();
-    if ((e = upload(o, (int2 **)&s.items, items.data(), items.size()))) return cuda_fail(c, e);
     // reciprocal
     s.n_runs = (int)t.runs.size() / 4;
     s.run_len = t.run_len;
@@ -192,8 +154,14 @@ int build_device(ewald_ctx *c) {
     s.e_self = t.e_self;
     s.e_bg = t.e_bg;
     s.e_II = t.e_II;
-    if ((e = (cudaError_t)configure_launch(s, t.precision, &c->cfg))) return cuda_fail(c, e);
-    return EWALD_OK;
+    // pair tiles of 32 x S particles per side; the largest item count (S = 1)
+    // sizes the batches' partial-sum buffers, so any tiling fits later
+    int S = t.n_mob >= 128 ? 4 : (t.n_mob >= 64 ? 2 : 1);
+    {
+        int nt1 = (t.n_mob + 31) / 32, nf1 = (t.n_fix + 31) / 32;
+        c->max_items = nt1 * (nt1 + 1) / 2 + nt1 * nf1;
+    }
+    return apply_tiling(c, S, t.sub_bits);
 }
 
 cudaEvent_t take_event(ewald_ctx *c) {
@@ -300,6 +268,70 @@ int run_energy(ewald_batch *b) {
     return e ? cuda_fail(c, (cudaError_t)e) : EWALD_OK;
 }
 
+// ---------------------------------------------------------------- autotune
+// Cache file: one JSON object {"entries": [{"key": K, "tile": T, "bits": B,
+// "ms": X}, ...]}, one entry per line, keyed by the system's shape.
+
+std::string tune_key(const ewald_ctx *c) {
+    const HostTables &t = c->t;
+    std::ostringstream k;
+    k.precision(9);
+    k << "dim=" << t.dim << " n=" << t.n_mob << " nfix=" << t.n_fix << " prec=" << t.precision
+      << " alpha=" << t.alpha << " rc=" << t.r_c << " gc=" << t.g_c << " A=";
+    for (int i = 0; i < t.dim; ++i)
+        for (int j = 0; j < t.dim; ++j) k << t.A[i][j] << (i == t.dim - 1 && j == t.dim - 1 ? "" : ",");
+    int dev = 0;
+    cudaDeviceProp pr;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&pr, dev) == cudaSuccess) k << " gpu=" << pr.name;
+    return k.str();
+}
+
+struct TuneEntry {
+    int tile, bits;
+    double ms;
+};
+
+std::map<std::string, TuneEntry> read_tune_cache(const char *path) {
+    std::map<std::string, TuneEntry> m;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        size_t a = line.find("\"key\": \"");
+        if (a == std::string::npos) continue;
+        a += 8;
+        size_t b = line.find('"', a);
+        if (b == std::string::npos) continue;
+        TuneEntry e{0, 0, 0};
+        size_t p;
+        if ((p = line.find("\"tile\": ", b)) != std::string::npos) e.tile = std::atoi(line.c_str() + p + 8);
+        if ((p = line.find("\"bits\": ", b)) != std::string::npos) e.bits = std::atoi(line.c_str() + p + 8);
+        if ((p = line.find("\"ms\": ", b)) != std::string::npos) e.ms = std::atof(line.c_str() + p + 6);
+        if (e.tile == 32 || e.tile == 64 || e.tile == 128) m[line.substr(a, b - a)] = e;
+    }
+    return m;
+}
+
+bool write_tune_cache(const char *path, const std::map<std::string, TuneEntry> &m) {
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    std::fprintf(f, "{\"entries\": [\n");
+    size_t i = 0;
+    for (auto &kv : m)
+        std::fprintf(f, "  {\"key\": \"%s\", \"tile\": %d, \"bits\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(),
+                     kv.second.tile, kv.second.bits, kv.second.ms, ++i < m.size() ? "," : "");
+    std::fprintf(f, "]}\n");
+    std::fclose(f);
+    return std::rename(tmp.c_str(), path) == 0;
+}
+
+bool tiling_allowed(const ewald_ctx *c, int S, int bits) {
+    const HostTables &t = c->t;
+    if (32 * S > std::max(32, 2 * t.n_mob)) return false;
+    int max_bits = t.dim == 3 ? 4 : 6;
+    return bits >= 0 && bits <= max_bits && subcell_bytes(t, bits) <= 48 * 1024;
+}
+
 bool ready(ewald_batch *b) {
     if (!b || !b->ctx) return false;
     if (!b->has_pos) {
@@ -353,6 +385,17 @@ int ewald_create(const ewald_desc *desc, void *cuda_stream, ewald_ctx **out) {
         ewald_destroy(c);
         return st;
     }
+    if (const char *path = std::getenv("EWALD_TUNE_CACHE")) {
+        auto cache = read_tune_cache(path);
+        auto it = cache.find(tune_key(c));
+        if (it != cache.end() && tiling_allowed(c, it->second.tile / 32, it->second.bits)) {
+            st = apply_tiling(c, it->second.tile / 32, it->second.bits);
+            if (st) {
+                ewald_destroy(c);
+                return st;
+            }
+        }
+    }
     *out = c;
     return EWALD_OK;
 }
@@ -389,6 +432,7 @@ int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
     i->n_g_half = (int)t.g2slot.size();
     i->n_images = (int)t.img.size() / 3;
     i->subcell_bits = t.sub_bits;
+    i->pair_tile = c->s.tile;
     i->max_candidates = t.cand_max;
     i->n_runs = (int)t.runs.size() / 4;
     i->run_len = t.run_len;
@@ -403,6 +447,11 @@ int ewald_get_gvectors(const ewald_ctx *c, int *nvec) {
     if (!c || !nvec) return EWALD_ERR_ARG;
     std::memcpy(nvec, c->t.gn.data(), c->t.gn.size() * sizeof(int));
     return EWALD_OK;
+}
+
+const char *ewald_last_error_message(const ewald_ctx *c) {
+    if (!c) return "no context";
+    return c->why.c_str();
 }
 
 int ewald_last_error(const ewald_ctx *c) {
@@ -432,7 +481,7 @@ int ewald_batch_create(ewald_ctx *c, int W, ewald_batch **out) {
     chk(dalloc(o, &d.pend_u, (size_t)W * 3));
     chk(dalloc(o, &d.acc_count, W));
     chk(dalloc(o, &d.resum_flag, W));
-    chk(dalloc(o, &d.part_real, (size_t)W * s.n_items));
+    chk(dalloc(o, &d.part_real, (size_t)W * std::max(c->max_items, s.n_items)));
     chk(dalloc(o, &d.part_recip, (size_t)W * s.n_gchunks));
     chk(dalloc(o, &d.e, W));
     chk(dalloc(o, &d.comp, (size_t)W * 5));
@@ -728,21 +777,27 @@ int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
 
     cudaError_t e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
     std::vector<void *> &o = m->dev;
-    auto chk = [&](cudaError_t x) { if (!e) e = x; };
+    const char *step = "stream";
+    auto chk = [&](cudaError_t x, const char *what = "") {
+        if (!e && x) {
+            e = x;
+            step = what;
+        }
+    };
     SysDev *d_sys = nullptr;
     BatchDev *d_bat = nullptr;
     int *d_bs = nullptr, *d_wb = nullptr;
     int4 *d_items = nullptr;
-    if (!e) chk(upload(o, &d_sys, sys.data(), sys.size()));
-    if (!e) chk(upload(o, &d_bat, bat.data(), bat.size()));
-    if (!e) chk(upload(o, &d_bs, bat_sys.data(), bat_sys.size()));
-    if (!e) chk(upload(o, &d_wb, wbase.data(), wbase.size()));
-    if (!e) chk(upload(o, &d_items, id.data(), id.size()));
+    if (!e) chk(upload(o, &d_sys, sys.data(), sys.size()), "upload systems");
+    if (!e) chk(upload(o, &d_bat, bat.data(), bat.size()), "upload batches");
+    if (!e) chk(upload(o, &d_bs, bat_sys.data(), bat_sys.size()), "upload map");
+    if (!e) chk(upload(o, &d_wb, wbase.data(), wbase.size()), "upload bases");
+    if (!e) chk(upload(o, &d_items, id.data(), id.size()), "upload items");
     MultiDev &md = m->m;
-    if (!e) chk(dalloc(o, &md.next, 1));
-    if (!e) chk(dalloc(o, &md.done, nw));
-    if (!e) chk(dalloc(o, &md.e_all, nw));
-    if (!e) chk(cudaMallocHost((void **)&m->pin, sizeof(double) * nw));
+    if (!e) chk(dalloc(o, &md.next, 1), "alloc");
+    if (!e) chk(dalloc(o, &md.done, nw), "alloc");
+    if (!e) chk(dalloc(o, &md.e_all, nw), "alloc");
+    if (!e) chk(cudaMallocHost((void **)&m->pin, sizeof(double) * nw), "pinned");
     md.sys = d_sys;
     md.bat = d_bat;
     md.bat_sys = d_bs;
@@ -751,8 +806,8 @@ int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
     md.n_items = (int)id.size();
     md.n_walkers = nw;
     m->smem = multi_energy_smem(sys, m->precision, &md.img_bytes);
-    if (!e) chk((cudaError_t)configure_multi(m->precision, m->smem, &m->grid));
-    if (!e) chk(cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming));
+    if (!e) chk((cudaError_t)configure_multi(m->precision, m->smem, &m->grid), "configure");
+    if (!e) chk(cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming), "event");
     for (size_t k = 0; k < m->ctxs.size() && !e; ++k) {
         cudaEvent_t ev;
         chk(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -761,20 +816,24 @@ int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
     // capture the launch (counter resets + kernel) once; every call replays it
     if (!e) {
         cudaGraph_t g = nullptr;
-        chk(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+        chk(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         if (!e) {
             int le = launch_multi_energy(md, m->precision, m->grid, m->smem, m->stream);
             cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
-            chk((cudaError_t)le);
-            chk(ce);
+            chk((cudaError_t)le, "launch in capture");
+            chk(ce, "end capture");
         }
-        if (!e) chk(cudaGraphInstantiate(&m->exec, g, 0));
+        if (!e) chk(cudaGraphInstantiate(&m->exec, g, 0), "instantiate");
         if (g) cudaGraphDestroy(g);
     }
     if (e) {
+        ewald_ctx *c0 = m->ctxs.empty() ? nullptr : m->ctxs[0];
+        if (c0)
+            c0->why = std::string("multi create, ") + step + ": " + cudaGetErrorName(e) + " (dynamic smem " +
+                      std::to_string(m->smem) + " B, grid " + std::to_string(m->grid) + ")";
         ewald_multi_destroy(m);
         cudaGetLastError();
-        return e == cudaErrorMemoryAllocation ? EWALD_ERR_OOM : EWALD_ERR_CUDA;
+        return fail(c0, e == cudaErrorMemoryAllocation ? EWALD_ERR_OOM : EWALD_ERR_CUDA);
     }
     *out = m;
     return EWALD_OK;
@@ -817,6 +876,80 @@ int ewald_multi_energy(ewald_multi *m, double *e_out, int on_device) {
         if (s2 && !st) st = s2;
     }
     return st;
+}
+
+int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *res) {
+    if (!b || !b->ctx) return EWALD_ERR_ARG;
+    if (!b->has_pos) return fail(b->ctx, EWALD_ERR_STATE, "positions not set");
+    ewald_ctx *c = b->ctx;
+    const std::string key = tune_key(c);
+    std::map<std::string, TuneEntry> cache;
+    if (cache_path) cache = read_tune_cache(cache_path);
+    ewald_tune_result r{};
+    auto it = cache.find(key);
+    if (it != cache.end() && tiling_allowed(c, it->second.tile / 32, it->second.bits)) {
+        int st = apply_tiling(c, it->second.tile / 32, it->second.bits);
+        if (st) return st;
+        r.pair_tile = it->second.tile;
+        r.subcell_bits = it->second.bits;
+        r.ms = it->second.ms;
+        r.from_cache = 1;
+        if (res) *res = r;
+        return EWALD_OK;
+    }
+    // time the real-space kernel on up to 512 of this batch's walkers
+    BatchDev view = b->b;
+    view.W = std::min(view.W, 512);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    int bestS = c->s.tile / 32, bestBits = c->s.sub_bits;
+    const int Ss[3] = {1, 2, 4};
+    for (int S : Ss)
+        for (int bits = 0; bits <= (c->t.dim == 3 ? 4 : 6); ++bits) {
+            if (!tiling_allowed(c, S, bits)) continue;
+            int st = apply_tiling(c, S, bits);
+            if (st) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+            double t_min = 1e300;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, c->stream);
+                int le = launch_real(c->s, view, c->t.precision, c->cfg, c->stream);
+                cudaEventRecord(e1, c->stream);
+                cudaError_t ce = cudaEventSynchronize(e1);
+                if (le || ce) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return cuda_fail(c, le ? (cudaError_t)le : ce);
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t_min = std::min(t_min, (double)ms);  // the first launch warms up
+            }
+            r.n_tried += 1;
+            if (t_min < best) {
+                best = t_min;
+                bestS = S;
+                bestBits = bits;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int st = apply_tiling(c, bestS, bestBits);
+    if (st) return st;
+    r.pair_tile = 32 * bestS;
+    r.subcell_bits = bestBits;
+    r.ms = best;
+    if (cache_path) {
+        cache[key] = TuneEntry{32 * bestS, bestBits, best};
+        write_tune_cache(cache_path, cache);
+    }
+    if (res) *res = r;
+    return EWALD_OK;
 }
 
 }  // extern "C"

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kSfacThreads)
 // -------------------------------------------------------------- real space
 // Persistent CTAs walk the (walker, tile pair) items; see real_item.
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kRealThreads) k_real(SysDev s, BatchDev b) {
+__global__ void __launch_bounds__(kRealThreads, 9) k_real(SysDev s, BatchDev b) {
     extern __shared__ __align__(32) unsigned char smem[];
     ImageSmem<R> ims;
     ims.carve(smem, s, DIM);
@@ -113,7 +113,7 @@ static size_t real_smem(const SysDev &s, int precision) {
 
 template <typename F>
 static cudaError_t allow_smem(F *f, size_t bytes) {
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return allow_max_smem(f, bytes);
 }
 
 size_t move_smem_bytes(const SysDev &s, int precision);  // move_kernels.cu

@@ -9,7 +9,7 @@
 //   rho_fix  : fixed particles' rho(G) per slot
 // and per walker batch:
 //   u        : [W][dim][stride] fixed-point fractional coordinates (uint64,
-//              2^64 = one lattice period); FP32 kernels use the top 32 bits
+//              2^64 = one lattice period); FP32 loops use the top 32 bits
 //   rho      : [W][run_len * n_runs] rho(G) (double2); slot = r * n_runs + run
 #pragma once
 #include <cuda_runtime.h>
@@ -48,12 +48,12 @@ struct SysDev {
     double alpha, rc2, coin2;
     float alpha_f, rc2_f, coin2_f;
     float alpha_lo_f, alpha2_f, alpha2_lo_f;  // alpha = alpha_f + alpha_lo_f, alpha^2 likewise
+    float close2_f;  // FP32 path: pairs closer than this (squared) get their R = 0 term in FP64
     // real space
     int n_img, sub_bits, cand_max;  // images [n_img + 1]: the last is a far sentinel
     const Img64 *img_d;
     const float4 *img_f;
     const unsigned short *cand;
-    const int *cand_len;
     int tile, n_mob_tiles, n_items;  // pair tiles (T = tile) and items per walker
     const int2 *items;               // (ti, tj); tj >= n_mob_tiles -> fixed tile tj - n_mob_tiles
     // reciprocal space
@@ -113,6 +113,8 @@ struct HostTables {
 // setup.cpp
 int build_tables(const ewald_desc *d, HostTables *t, std::string *why);
 int pick_subcells(HostTables *t, int max_bytes);
+int set_subcells(HostTables *t, int bits);
+size_t subcell_bytes(const HostTables &t, int bits);
 
 // kernels.cu launchers (return cudaError_t as int)
 struct LaunchCfg {

@@ -88,10 +88,10 @@ int configure_multi(int precision, size_t smem, int *grid) {
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e) return e;
     if (precision == EWALD_FP64) {
-        if ((e = cudaFuncSetAttribute(k_multi_energy<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        if ((e = allow_max_smem(k_multi_energy<double>, smem))) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_energy<double>, kMultiThreads, smem);
     } else {
-        if ((e = cudaFuncSetAttribute(k_multi_energy<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        if ((e = allow_max_smem(k_multi_energy<float>, smem))) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_energy<float>, kMultiThreads, smem);
     }
     if (e) return e;

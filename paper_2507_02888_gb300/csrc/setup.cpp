@@ -183,6 +183,18 @@ static int build_cand(const HostTables &t, int bits, std::vector<unsigned short>
     return longest;
 }
 
+int set_subcells(HostTables *t, int bits) {
+    t->sub_bits = bits;
+    t->cand_max = build_cand(*t, bits, &t->cand, &t->cand_len);
+    return t->cand_max;
+}
+
+// Bytes of shared memory the candidate lists of 2^bits cells per axis need.
+size_t subcell_bytes(const HostTables &t, int bits) {
+    int n_sub = 1 << (bits * t.dim);
+    return (size_t)n_sub * build_cand(t, bits, nullptr, nullptr) * 2;
+}
+
 // Choose the number of displacement cells: the shortest longest-list whose
 // table fits in max_bytes of shared memory.
 int pick_subcells(HostTables *t, int max_bytes) {

@@ -36,11 +36,16 @@ class Desc(ctypes.Structure):
                 ("resum_every", _c_int)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("pair_tile", _c_int), ("subcell_bits", _c_int), ("ms", _c_double), ("n_tried", _c_int),
+                ("from_cache", _c_int)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("dim", _c_int), ("n_mobile", _c_int), ("n_fixed", _c_int), ("precision", _c_int),
                 ("alpha", _c_double), ("r_cutoff", _c_double), ("g_cutoff", _c_double),
                 ("volume", _c_double), ("n_g_half", _c_int), ("n_images", _c_int),
-                ("subcell_bits", _c_int), ("max_candidates", _c_int), ("n_runs", _c_int),
+                ("subcell_bits", _c_int), ("pair_tile", _c_int), ("max_candidates", _c_int), ("n_runs", _c_int),
                 ("run_len", _c_int), ("e_madelung", _c_double), ("e_self", _c_double),
                 ("e_background", _c_double), ("e_fixed_real", _c_double)]
 
@@ -72,6 +77,7 @@ SIGNATURES = [
     ("ewald_get_gvectors", _c_int, [_vp, _vp]),
     ("ewald_last_error", _c_int, [_vp]),
     ("ewald_strerror", ctypes.c_char_p, [_c_int]),
+    ("ewald_last_error_message", ctypes.c_char_p, [_vp]),
     ("ewald_batch_create", _c_int, [_vp, _c_int, ctypes.POINTER(_vp)]),
     ("ewald_batch_destroy", None, [_vp]),
     ("ewald_batch_set_positions", _c_int, [_vp, _vp, _c_int]),
@@ -86,6 +92,7 @@ SIGNATURES = [
     ("ewald_multi_create", _c_int, [_vp, _c_int, ctypes.POINTER(_vp)]),
     ("ewald_multi_energy", _c_int, [_vp, _vp, _c_int]),
     ("ewald_multi_destroy", None, [_vp]),
+    ("ewald_autotune", _c_int, [_vp, ctypes.c_char_p, _vp]),
     ("ewald_set_timing", _c_int, [_vp, _c_int]),
     ("ewald_get_timing", _c_int, [_vp, _vp, _vp]),
 ]
@@ -117,7 +124,10 @@ def load(build_if_missing=True):
 
 def _check(code, ctx=None):
     if code != 0:
-        raise EwaldError(code, _lib.ewald_strerror(code).decode())
+        what = _lib.ewald_strerror(code).decode()
+        if ctx is not None and getattr(ctx, "_h", None):
+            what += " - " + _lib.ewald_last_error_message(ctx._h).decode()
+        raise EwaldError(code, what)
 
 
 def _f64(a, n=None):
@@ -215,7 +225,7 @@ class Batch:
         self.ctx = ctx
         self.W = int(n_walkers)
         h = _vp()
-        _check(_lib.ewald_batch_create(ctx._h, self.W, ctypes.byref(h)))
+        _check(_lib.ewald_batch_create(ctx._h, self.W, ctypes.byref(h)), ctx)
         self._h = h
         _live_batches.add(self)
 
@@ -224,13 +234,13 @@ class Batch:
         if not _is_dev(pos):
             pos = _f64(pos, self.W * self.ctx.n_mobile * self.ctx.dim)
         p, dev = _ptr(pos)
-        _check(_lib.ewald_batch_set_positions(self._h, p, dev))
+        _check(_lib.ewald_batch_set_positions(self._h, p, dev), self.ctx)
 
     def get_positions(self, out=None):
         if out is None:
             out = np.zeros((self.W, self.ctx.n_mobile, self.ctx.dim))
         p, dev = _ptr(out)
-        _check(_lib.ewald_batch_get_positions(self._h, p, dev))
+        _check(_lib.ewald_batch_get_positions(self._h, p, dev), self.ctx)
         return out
 
     # -- energies
@@ -238,14 +248,14 @@ class Batch:
         if out is None:
             out = np.zeros(self.W)
         p, dev = _ptr(out)
-        _check(_lib.ewald_energy(self._h, p, dev))
+        _check(_lib.ewald_energy(self._h, p, dev), self.ctx)
         return out
 
     def components(self, out=None):
         if out is None:
             out = np.zeros((self.W, 5))
         p, dev = _ptr(out)
-        _check(_lib.ewald_energy_components(self._h, p, dev))
+        _check(_lib.ewald_energy_components(self._h, p, dev), self.ctx)
         return out
 
     # -- moves
@@ -262,28 +272,35 @@ class Batch:
         pk, dev = _ptr(k)
         pr, _ = _ptr(r_new)
         po, _ = _ptr(out)
-        _check(_lib.ewald_propose_move(self._h, pk, pr, po, dev))
+        _check(_lib.ewald_propose_move(self._h, pk, pr, po, dev), self.ctx)
         return out
 
     def accept(self, accept):
         if not _is_dev(accept):
             accept = np.ascontiguousarray(np.asarray(accept, dtype=np.uint8))
         p, dev = _ptr(accept)
-        _check(_lib.ewald_accept_move(self._h, p, dev))
+        _check(_lib.ewald_accept_move(self._h, p, dev), self.ctx)
 
     def resum(self):
-        _check(_lib.ewald_resum(self._h))
+        _check(_lib.ewald_resum(self._h), self.ctx)
 
     def rho(self, out=None):
         n = self.ctx.info()["n_g_half"]
         if out is None:
             out = np.zeros((self.W, n, 2))
         p, dev = _ptr(out)
-        _check(_lib.ewald_batch_get_rho(self._h, p, dev))
+        _check(_lib.ewald_batch_get_rho(self._h, p, dev), self.ctx)
         return out
 
     def sync(self):
-        _check(_lib.ewald_batch_sync(self._h))
+        _check(_lib.ewald_batch_sync(self._h), self.ctx)
+
+    def autotune(self, cache_path=None):
+        """Pick the fastest real-space tiling for this batch's system (see ewald_autotune)."""
+        r = TuneResult()
+        _check(_lib.ewald_autotune(self._h, cache_path.encode() if cache_path else None,
+                                   ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in r._fields_}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -304,7 +321,7 @@ class Multi:
         self.batches = list(batches)
         arr = (_vp * len(self.batches))(*[b._h for b in self.batches])
         h = _vp()
-        _check(_lib.ewald_multi_create(arr, len(self.batches), ctypes.byref(h)))
+        _check(_lib.ewald_multi_create(arr, len(self.batches), ctypes.byref(h)), self.batches[0].ctx)
         self._h = h
         self.W = sum(b.W for b in self.batches)
         _live_multis.add(self)
@@ -314,7 +331,7 @@ class Multi:
         if out is None:
             out = np.zeros(self.W)
         p, dev = _ptr(out)
-        _check(_lib.ewald_multi_energy(self._h, p, dev))
+        _check(_lib.ewald_multi_energy(self._h, p, dev), self.batches[0].ctx)
         return out
 
     def close(self):
