@@ -224,6 +224,24 @@ typedef struct {
 } ewald_tune_result;
 int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *res);
 
+/* Full energies without any device allocation at call time.  Meant for
+ * callers that cannot call cudaMalloc while they compute (a host framework
+ * that owns all device memory through its own pool, a CUDA-graph capture
+ * that must not allocate, an embedded code that reserves memory up front).
+ * pos [n_walkers][N][dim] and e_out [n_walkers] are device arrays of the
+ * caller; status_out (device int, may be NULL) receives 0, or bit 1 for
+ * coincident particles and bit 4 for a non-finite position.  All
+ * intermediates live in one static device array of 32 MiB that every GPU
+ * which loads the library holds until the process exits; n_walkers beyond
+ * what fits for this system returns EWALD_ERR_OOM with the limit in
+ * ewald_last_error_message.  Work is queued on the context's stream and the
+ * call returns without waiting.  Calls that overlap on the GPU (other
+ * streams, other contexts, other threads) share that array and race: keep
+ * them ordered.  The first call on each device looks up the array's device
+ * address; make that first call before any stream capture.  There is no
+ * counterpart in the paper: this is a deployment convenience. */
+int ewald_energy_noalloc(ewald_ctx *ctx, const double *pos, int n_walkers, double *e_out, int *status_out);
+
 /* Kernel timers of a context (in the spirit of the paper's per-subroutine
  * timers, Sec. 3.2).  When enabled, every kernel the context launches is
  * bracketed by CUDA events on its stream.  ewald_get_timing synchronises

@@ -1,5 +1,5 @@
 // Private definitions of the C ABI objects, shared by the files that
-// implement entry points (capi.cu, serve.cu).
+// implement entry points (capi.cu, serve.cu, noalloc.cu).
 #pragma once
 #include <string>
 #include <utility>
