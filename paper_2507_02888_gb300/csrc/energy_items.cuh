@@ -23,7 +23,7 @@ __host__ __device__ inline size_t sfac_bytes(const SysDev &s, int precision, int
 __host__ __device__ inline size_t real_work_bytes(const SysDev &s, int precision, int warps) {
     size_t part = precision == EWALD_FP64 ? sizeof(Part<double>) : sizeof(Part<float>);
     size_t qe = precision == EWALD_FP64 ? sizeof(QE<double>) : sizeof(QE<float>);
-    return 2 * align16(s.tile * part) + align16((size_t)warps * kQueueCap * qe) + align16(16 * sizeof(double));
+    return 2 * align16(s.tile * part) + align16((size_t)warps * kQueueCap * qe) + align16(kRealUnits * sizeof(double));
 }
 
 // One CTA; blockDim.x threads, each owning one run of <= kRunLen consecutive
@@ -139,15 +139,18 @@ __device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, 
 }
 
 // One CTA, any number of warps.  The tile pair's particles are staged in
-// shared memory; each warp takes 32 x 32 sub-tiles (lane = i, loop over j),
-// diagonal tiles only their upper triangle.  Images inside the cutoff go
-// through the warp queue.  Every sub-tile is summed on its own and the
-// sub-tile sums are added in sub-tile order in FP64, so the item's partial
-// sum does not depend on how many warps the CTA has.
-// ims must already hold this system's images; work is this item's scratch.
+// shared memory; each warp takes units of a 32 x 32 sub-tile (lane = i,
+// loop over j), diagonal tiles only their upper triangle.  A unit is the
+// whole sub-tile (jsplit = 1) or one of jsplit equal slices of its 32 j, so
+// that CTAs with more warps than sub-tiles keep every warp busy.  Images
+// inside the cutoff go through the warp queue.  Every unit is summed on its
+// own and the unit sums are added in unit order in FP64, so the item's
+// partial sum depends on jsplit but not on how many warps the CTA has.
+// ims must already hold this system's images; work is this item's scratch
+// (its reduction array holds kRealUnits doubles: nst * jsplit must fit).
 template <typename R, int DIM>
 __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, const ImageSmem<R> &ims,
-                          unsigned char *work) {
+                          unsigned char *work, int jsplit = 1) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     size_t off = 0;
     Part<R> *ti = (Part<R> *)(work + off);
@@ -174,7 +177,9 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
     const typename FP<R>::K tk = FP<R>::term_consts(s);
     const bool diag = !fixedj && tt.x == tt.y;
     const int nst = diag ? S * (S + 1) / 2 : S * S;
-    for (int st = warp; st < nst; st += nw) {
+    const int nunits = nst * jsplit, jlen = 32 / jsplit;
+    for (int u = warp; u < nunits; u += nw) {
+        const int st = u / jsplit, j_lo = (u - st * jsplit) * jlen;
         int a, c;
         if (diag) {
             a = 0;
@@ -191,19 +196,19 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
         const Part<R> pi = ti[a * 32 + lane];
         const bool vi = i0 + a * 32 + lane < s.n_mob;
         Acc<R> acc;
-        for (int jj = 0; jj < 32; ++jj) {
+        for (int jj = j_lo; jj < j_lo + jlen; ++jj) {
             const int lj = c * 32 + jj;
             const bool v = vi && (j0 + lj < nj) && (!(diag && a == c) || lane < jj);
             pair_images<R, DIM>(s, pi, tj[lj], v, R(1), ims.img, ims.cand, wq, acc, lane);
         }
         wq.drain(acc, tk, lane);
         const double v = warp_sum(acc.get());
-        if (lane == 0) red[st] = v;
+        if (lane == 0) red[u] = v;
     }
     __syncthreads();
     if (tid == 0) {
         double t = 0;
-        for (int k = 0; k < nst; ++k) t += red[k];
+        for (int k = 0; k < nunits; ++k) t += red[k];
         b.part_real[(size_t)w * s.n_items + p] = t;
     }
 }

@@ -28,6 +28,7 @@ constexpr int kQueueCap = 64;          // per-warp queue of accepted (r^2, weigh
 constexpr int kSfacThreads = 256;      // threads (= runs) per structure-factor CTA
 constexpr int kMoveThreads = 256;      // threads per walker in propose / accept
 constexpr int kRunLen = 8;             // maximum G run length (compile-time)
+constexpr int kRealUnits = 16;         // work units (sub-tiles x j slices) of one pair item, at most
 
 // FP64 image vector (x, y, z, unused), 32-byte aligned for two 16-byte loads.
 struct __align__(32) Img64 {

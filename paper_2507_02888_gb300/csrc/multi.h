@@ -7,6 +7,8 @@
 namespace ewald {
 
 constexpr int kMultiThreads = 256;
+// resident CTAs per SM the register budget is sized for (FP32, FP64 path)
+constexpr int kMultiMinBlocks32 = 3, kMultiMinBlocks64 = 2;
 enum : int { kItemSfac = 0, kItemReal = 1 };
 
 struct MultiDev {

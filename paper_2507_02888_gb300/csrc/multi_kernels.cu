@@ -22,8 +22,18 @@ __device__ inline void cta_copy(T *dst, const T *src) {
     for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
 }
 
+// j slices per 32 x 32 sub-tile of a pair item, so that the item has at
+// least as many work units as the CTA has warps (a property of the system
+// alone: results do not depend on the other systems of the launch)
+__device__ inline int multi_jsplit(const SysDev &s) {
+    const int S = s.tile / 32, per = S * S;
+    int js = 1;
+    while (per * js < kMultiThreads / 32 && js < 32) js *= 2;
+    return js;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(kMultiThreads) k_multi_energy(MultiDev m) {
+__global__ void __launch_bounds__(kMultiThreads, sizeof(R) == 4 ? kMultiMinBlocks32 : kMultiMinBlocks64) k_multi_energy(MultiDev m) {
     extern __shared__ __align__(32) unsigned char smem[];
     __shared__ SysDev ss;
     __shared__ BatchDev sb;
@@ -53,8 +63,9 @@ __global__ void __launch_bounds__(kMultiThreads) k_multi_energy(MultiDev m) {
             if (ss.dim == 3) sfac_item<R, 3>(ss, sb, d.z, d.w, ss.sfac_te, true, work);
             else sfac_item<R, 2>(ss, sb, d.z, d.w, ss.sfac_te, true, work);
         } else {
-            if (ss.dim == 3) real_item<R, 3>(ss, sb, d.z, d.w, ims, work);
-            else real_item<R, 2>(ss, sb, d.z, d.w, ims, work);
+            const int js = multi_jsplit(ss);
+            if (ss.dim == 3) real_item<R, 3>(ss, sb, d.z, d.w, ims, work, js);
+            else real_item<R, 2>(ss, sb, d.z, d.w, ims, work, js);
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -54,9 +54,10 @@ def test_multi_equals_single_batches(ew, prec):
     m = ew.Multi(bs)
     e1 = m.energy().copy()
     e2 = m.energy().copy()       # graph replay gives the same bits as the first launch
-    # same items as the single-batch kernels, summed in the same fixed order;
-    # two differently compiled kernels can still round FP32 steps differently
-    tol = 1e-14 if prec == "fp64" else 1e-6
+    # the same terms as the single-batch kernels; the persistent kernel splits
+    # each 32 x 32 sub-tile into j slices to keep its 8 warps busy, so its
+    # partial sums are added in another (fixed) order: equal to rounding
+    tol = 1e-13 if prec == "fp64" else 1e-6
     assert np.all(np.abs(e1 - alone) <= tol * floor), np.max(np.abs(e1 - alone) / floor)
     assert np.array_equal(e1, e2)
     # each batch is still usable on its own afterwards
