@@ -69,7 +69,9 @@ typedef struct {
     double gamma;                /* alpha of erfc(alpha r); <= 0 picks a balanced alpha */
     double g_cutoff;             /* |G| cutoff; <= 0: exp(-G^2/4alpha^2) (3D) or
                                     erfc(G/2alpha) (2D) reaches 1e-16 */
-    double r_cutoff;             /* real-space cutoff; <= 0: erfc(alpha r) reaches 1e-16 */
+    double r_cutoff;             /* real-space cutoff; <= 0: erfc(alpha r) reaches 1e-16
+                                    (EWALD_FP64) or 1e-10 (EWALD_MIXED: images beyond
+                                    add less than FP32 resolves; see ewald_get_info) */
     int precision;               /* ewald_precision */
     int resum_every;             /* accepted moves between rho(G) rebuilds; 0 -> 64 */
 } ewald_desc;

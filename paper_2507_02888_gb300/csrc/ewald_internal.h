@@ -24,10 +24,14 @@ namespace ewald {
 
 constexpr int kRealWarps = 4;          // warps per real-space CTA
 constexpr int kRealThreads = 32 * kRealWarps;
-constexpr int kQueueCap = 64;          // per-warp queue of accepted (r^2, weight) terms
+constexpr int kRealMinBlocks = 8;      // resident real-space CTAs per SM the registers are sized for
+constexpr int kQueueCap = 96;          // per-warp queue of accepted (r^2, weight) terms
 constexpr int kSfacThreads = 256;      // threads (= runs) per structure-factor CTA
 constexpr int kMoveThreads = 256;      // threads per walker in propose / accept
 constexpr int kRunLen = 8;             // maximum G run length (compile-time)
+// default real-space cutoff of the mixed path: erfc(alpha r_c) = kMixedRealTol
+// (the FP64 path and every G cutoff use 1e-16)
+constexpr double kMixedRealTol = 1e-10;
 constexpr int kRealUnits = 16;         // work units (sub-tiles x j slices) of one pair item, at most
 
 // FP64 image vector (x, y, z, unused), 32-byte aligned for two 16-byte loads.

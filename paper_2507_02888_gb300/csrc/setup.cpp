@@ -4,8 +4,9 @@
 //
 // Builds, from the lattice, the charges and alpha:
 //   - the reciprocal basis b_k (a_i . b_j = 2 pi delta_ij) and the volume;
-//   - the cutoffs (erfc(alpha r_c) = 1e-16; exp(-G^2/4alpha^2) = 1e-16 in 3D,
-//     erfc(G/2alpha) = 1e-16 in 2D) unless the caller gives them;
+//   - the cutoffs (erfc(alpha r_c) = 1e-16, or kMixedRealTol in the mixed
+//     path; exp(-G^2/4alpha^2) = 1e-16 in 3D, erfc(G/2alpha) = 1e-16 in 2D)
+//     unless the caller gives them;
 //   - the G vectors of one half-space (one of each +-G pair), grouped in rows
 //     of consecutive n1 and split into runs for the structure-factor kernel,
 //     with weights 2 C f(G) (paper Eq. (3) and Eq. (5) at z = 0);
@@ -386,8 +387,15 @@ int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
     int st = setup_lattice(t, d->lattice, why);
     if (st) return st;
 
+    // Cutoff tolerances.  The G side is 1e-16 in both precisions (the
+    // reciprocal sum is cheap and sets the G count).  The real-space side is
+    // 1e-16 in FP64; the mixed path re-expresses it for FP32 (as Sec. 6.1
+    // does with CASINO's hard-wired tolerances): kMixedRealTol, far below
+    // FP32 resolution but well above 1e-16, so that the pair sum skips the
+    // images whose terms could not change an FP32 result.
     const double tol = 1e-16;
     double x_r = inverse_erfc(tol);
+    const double x_rr = d->precision == EWALD_MIXED ? inverse_erfc(kMixedRealTol) : x_r;
     if (d->gamma > 0) {
         t->alpha = d->gamma;
     } else {
@@ -405,7 +413,7 @@ int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
             t->alpha = gc / (2 * x_r);
         }
     }
-    t->r_c = d->r_cutoff > 0 ? d->r_cutoff : x_r / t->alpha;
+    t->r_c = d->r_cutoff > 0 ? d->r_cutoff : x_rr / t->alpha;
     t->g_c = d->g_cutoff > 0 ? d->g_cutoff
                              : (dim == 3 ? 2 * t->alpha * std::sqrt(-std::log(tol)) : 2 * t->alpha * x_r);
     // guard against cutoffs that would need absurd tables

@@ -17,6 +17,7 @@ from paper_2507_02888_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "mixed": 1e-6}
+MIXED_REAL_TOL = 1e-10   # default real-space cutoff tolerance of the mixed path
 
 
 @pytest.fixture(scope="module")
@@ -112,11 +113,14 @@ def test_energy_matches_oracle(ew, case, prec):
         assert np.all(np.abs(comp[walker] - c_o) <= TOL[prec] * np.maximum(np.abs(c_o), floor)), (comp[walker], c_o)
 
 
-def test_cutoffs_match_oracle_definition(ew):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cutoffs_match_oracle_definition(ew, prec):
     w = small_case("fcc100", 1)
-    ctx, _ = make(ew, w, "fp64")
+    ctx, _ = make(ew, w, prec)
     info = ctx.info()
     rc, gc = oracle.cutoffs(3, w["alpha"])
+    if prec == "mixed":                                # real space at erfc(alpha r_c) = 1e-10
+        rc, _ = oracle.cutoffs(3, w["alpha"], MIXED_REAL_TOL)
     assert abs(info["r_cutoff"] / rc - 1) < 1e-9 and abs(info["g_cutoff"] / gc - 1) < 1e-9
     assert 2 * info["n_g_half"] == oracle.gcount(3, w["lattice"], gc)
 
@@ -269,11 +273,14 @@ FULL = [("heg3d_fcc_n1024", [0, 2047, 4095]), ("heg2d_hex_n338", [0, 1500]),
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("name,sample", FULL)
 def test_full_size_sampled_walkers(ew, name, sample, prec):
+    """Each path with its default cutoffs against the oracle at the definition's
+    cutoffs (1e-16 in both spaces): for the mixed path this includes the
+    real-space images it leaves out beyond erfc(alpha r_c) = 1e-10."""
     w = I.workload(name)
     ctx, b = make(ew, w, prec)
-    info = ctx.info()
     e = b.energy()
     assert np.all(np.isfinite(e))
+    rc, gc = oracle.cutoffs(w["dim"], w["alpha"])
     for walker in sample:
-        e_o, c_o = oracle_energy(w, walker, info["r_cutoff"], info["g_cutoff"])
+        e_o, c_o = oracle_energy(w, walker, rc, gc)
         assert abs(e[walker] - e_o) <= TOL[prec] * max(abs(e_o), 1e-2 * scale(c_o)), (walker, e[walker], e_o)
