@@ -116,11 +116,18 @@ const char *ewald_last_error_message(const ewald_ctx *ctx);
 
 /* Walker batches.  A batch owns the walkers' positions (fixed-point
  * fractional coordinates), their rho(G) and the pending moves.  Before the
- * first energy or move the positions must be set. */
+ * first energy or move the positions must be set.
+ *
+ * Host arrays (on_device = 0) may be ordinary or page-locked memory
+ * (cudaMallocHost, cudaHostRegister); page-locked arrays are copied by DMA
+ * directly, others through the batch's staging buffer.  Either way the call
+ * has finished with the caller's array when it returns. */
 int ewald_batch_create(ewald_ctx *ctx, int n_walkers, ewald_batch **out);
 void ewald_batch_destroy(ewald_batch *b);
 /* pos: [W][N][dim] Cartesian.  Positions are stored wrapped into the cell;
- * get_positions returns the wrapped positions. */
+ * get_positions returns the wrapped positions.  rho(G) follows new
+ * positions: it is rebuilt by the next energy, or before the next call that
+ * reads it (propose, resum, get_rho). */
 int ewald_batch_set_positions(ewald_batch *b, const double *pos, int on_device);
 int ewald_batch_get_positions(ewald_batch *b, double *pos, int on_device);
 /* Synchronise the context's stream and report errors raised by kernels. */

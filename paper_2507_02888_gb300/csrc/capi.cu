@@ -221,6 +221,17 @@ int sync_status(ewald_batch *b) {
     return fail(c, EWALD_ERR_ARG, st & ST_BAD_INDEX ? "move index or position invalid" : "non-finite position");
 }
 
+// Page-locked host memory (cudaMallocHost / cudaHostRegister): copied by
+// DMA directly, without the staging buffer.
+bool is_pinned_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // not a pointer CUDA knows: ordinary host memory
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 // Copy n bytes of device memory to a host or device destination.
 int copy_out(ewald_batch *b, void *dst, const void *src, size_t n, int on_device) {
     ewald_ctx *c = b->ctx;
@@ -228,6 +239,11 @@ int copy_out(ewald_batch *b, void *dst, const void *src, size_t n, int on_device
     if (on_device) {
         e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, c->stream);
         return e ? cuda_fail(c, e) : EWALD_OK;
+    }
+    if (is_pinned_host(dst)) {
+        e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->stream);
+        if (e) return cuda_fail(c, e);
+        return sync_status(b);
     }
     // status word first, then the payload behind it in the pinned buffer
     char *pin = (char *)b->pin;
@@ -241,14 +257,16 @@ int copy_out(ewald_batch *b, void *dst, const void *src, size_t n, int on_device
 // Stage a host array into device scratch; returns the device pointer.
 const void *copy_in(ewald_batch *b, const void *src, size_t n, void *dscratch, int *err) {
     ewald_ctx *c = b->ctx;
+    const bool direct = is_pinned_host(src);
     char *pin = (char *)b->pin + 16;
-    std::memcpy(pin, src, n);
-    cudaError_t e = cudaMemcpyAsync(dscratch, pin, n, cudaMemcpyHostToDevice, c->stream);
+    if (!direct) std::memcpy(pin, src, n);
+    cudaError_t e = cudaMemcpyAsync(dscratch, direct ? src : pin, n, cudaMemcpyHostToDevice, c->stream);
     if (e) {
         *err = cuda_fail(c, e);
         return nullptr;
     }
-    // the pinned buffer is reused by the next call: wait for the copy
+    // the staging buffer (or the caller's array) is reused after the call
+    // returns: wait for the copy
     if ((e = cudaStreamSynchronize(c->stream))) {
         *err = cuda_fail(c, e);
         return nullptr;
@@ -265,7 +283,20 @@ int run_energy(ewald_batch *b) {
     int e = timed(c, KT_SFAC, [&] { return launch_sfac(c->s, b->b, p, c->cfg, nullptr, c->stream); });
     if (!e) e = timed(c, KT_REAL, [&] { return launch_real(c->s, b->b, p, c->cfg, c->stream); });
     if (!e) e = timed(c, KT_COMBINE, [&] { return launch_combine(c->s, b->b, c->stream); });
-    return e ? cuda_fail(c, (cudaError_t)e) : EWALD_OK;
+    if (e) return cuda_fail(c, (cudaError_t)e);
+    b->rho_stale = false;
+    return EWALD_OK;
+}
+
+// rho(G) is rebuilt lazily after new positions: by the next energy, or here
+// by the first call that reads it without one.
+int ensure_rho(ewald_batch *b) {
+    if (!b->rho_stale) return EWALD_OK;
+    ewald_ctx *c = b->ctx;
+    int e = timed(c, KT_RESUM, [&] { return launch_sfac(c->s, b->b, c->t.precision, c->cfg, nullptr, c->stream); });
+    if (e) return cuda_fail(c, (cudaError_t)e);
+    b->rho_stale = false;
+    return EWALD_OK;
 }
 
 // ---------------------------------------------------------------- autotune
@@ -542,9 +573,7 @@ int ewald_batch_set_positions(ewald_batch *b, const double *pos, int on_device) 
     if (e) return cuda_fail(c, (cudaError_t)e);
     b->has_pos = true;
     b->has_pending = false;
-    // rho(G) follows the new positions
-    e = timed(c, KT_RESUM, [&] { return launch_sfac(c->s, b->b, c->t.precision, c->cfg, nullptr, c->stream); });
-    if (e) return cuda_fail(c, (cudaError_t)e);
+    b->rho_stale = true;  // rho(G) follows the new positions at its next use
     if (!on_device) return sync_status(b);
     return EWALD_OK;
 }
@@ -605,6 +634,7 @@ int ewald_propose_move(ewald_batch *b, const int *k, const double *r_new, double
         dr = b->d_rnew;
     }
     double *dde = on_device ? de_out : b->d_de;
+    if (int r = ensure_rho(b)) return r;
     int e = timed(c, KT_PROPOSE, [&] { return launch_propose(c->s, b->b, c->t.precision, c->cfg, dk, dr, dde, c->stream); });
     if (e) return cuda_fail(c, (cudaError_t)e);
     b->has_pending = true;
@@ -634,14 +664,14 @@ int ewald_accept_move(ewald_batch *b, const unsigned char *accept, int on_device
 
 int ewald_resum(ewald_batch *b) {
     if (!ready(b)) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
-    ewald_ctx *c = b->ctx;
-    int e = timed(c, KT_RESUM, [&] { return launch_sfac(c->s, b->b, c->t.precision, c->cfg, nullptr, c->stream); });
-    return e ? cuda_fail(c, (cudaError_t)e) : EWALD_OK;
+    b->rho_stale = true;
+    return ensure_rho(b);
 }
 
 int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device) {
     if (!ready(b) || !rho_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     ewald_ctx *c = b->ctx;
+    if (int r = ensure_rho(b)) return r;
     double *dst = on_device ? rho_out : b->d_io;
     int e = launch_rho_out(c->s, b->b, c->d_g2slot, dst, c->stream);
     if (e) return cuda_fail(c, (cudaError_t)e);
@@ -865,7 +895,10 @@ int ewald_multi_energy(ewald_multi *m, double *e_out, int on_device) {
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
     if (!e) e = cudaEventRecord(m->ev_out, m->stream);
     for (size_t k = 0; k < m->ctxs.size() && !e; ++k) e = cudaStreamWaitEvent(m->ctxs[k]->stream, m->ev_out, 0);
-    for (ewald_batch *b : m->batches) b->has_pending = false;
+    for (ewald_batch *b : m->batches) {
+        b->has_pending = false;
+        b->rho_stale = false;  // the launch rebuilt every batch's rho(G)
+    }
     if (e) return cuda_fail(m->ctxs[0], e);
     if (on_device) return EWALD_OK;
     if ((e = cudaStreamSynchronize(m->stream))) return cuda_fail(m->ctxs[0], e);

@@ -36,6 +36,7 @@ struct ewald_batch {
     ewald::BatchDev b{};
     std::vector<void *> dev;
     bool has_pos = false, has_pending = false;
+    bool rho_stale = false;  // positions changed since rho(G) was last built
     bool counted = false;  // included in ctx->n_batches
     // host-I/O staging: pinned host buffer and device scratch for host inputs
     void *pin = nullptr;

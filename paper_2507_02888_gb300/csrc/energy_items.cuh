@@ -23,7 +23,8 @@ __host__ __device__ inline size_t sfac_bytes(const SysDev &s, int precision, int
 __host__ __device__ inline size_t real_work_bytes(const SysDev &s, int precision, int warps) {
     size_t part = precision == EWALD_FP64 ? sizeof(Part<double>) : sizeof(Part<float>);
     size_t qe = precision == EWALD_FP64 ? sizeof(QE<double>) : sizeof(QE<float>);
-    return 2 * align16(s.tile * part) + align16((size_t)warps * kQueueCap * qe) + align16(kRealUnits * sizeof(double));
+    return 2 * align16(s.tile * part) + align16((size_t)warps * kQueueCap * qe) +
+           align16((size_t)warps * kCloseCap * sizeof(unsigned)) + align16(kRealUnits * sizeof(double));
 }
 
 // One CTA; blockDim.x threads, each owning one run of <= kRunLen consecutive
@@ -159,6 +160,8 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
     off += align16(s.tile * sizeof(Part<R>));
     QE<R> *qbase = (QE<R> *)(work + off);
     off += align16((size_t)nw * kQueueCap * sizeof(QE<R>));
+    unsigned *cbase = (unsigned *)(work + off);
+    off += align16((size_t)nw * kCloseCap * sizeof(unsigned));
     double *red = (double *)(work + off);
 
     const int S = s.tile / 32;
@@ -193,15 +196,43 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
             a = st / S;
             c = st - a * S;
         }
-        const Part<R> pi = ti[a * 32 + lane];
-        const bool vi = i0 + a * 32 + lane < s.n_mob;
+        const int li = a * 32 + lane;
+        const Part<R> pi = ti[li];
+        const bool vi = i0 + li < s.n_mob;
+        auto valid = [&](int jj) { return vi && (j0 + c * 32 + jj < nj) && (!(diag && a == c) || lane < jj); };
         Acc<R> acc;
+        CloseList cl{cbase + warp * kCloseCap, 0};
         for (int jj = j_lo; jj < j_lo + jlen; ++jj) {
             const int lj = c * 32 + jj;
-            const bool v = vi && (j0 + lj < nj) && (!(diag && a == c) || lane < jj);
-            pair_images<R, DIM>(s, pi, tj[lj], v, R(1), ims.img, ims.cand, wq, acc, lane);
+            pair_images<R, DIM, true>(s, pi, tj[lj], valid(jj), R(1), ims.img, ims.cand, wq, acc, lane, &cl,
+                                      ((unsigned)li << 16) | (unsigned)lj);
         }
         wq.drain(acc, tk, lane);
+        if constexpr (sizeof(R) == 4) {
+            if (cl.n > 0) {  // uniform over the warp; close pairs are rare
+                __syncwarp();
+                if (cl.n <= kCloseCap) {
+                    for (int e = lane; e < cl.n; e += 32) {
+                        const unsigned id = cl.e[e];
+                        const Part<R> &pa = ti[id >> 16], &pb = tj[id & 0xffffu];
+                        acc.add64(close_pair_term<DIM>(s, pa, pb, (double)(R(1) * pa.q * pb.q), b.status));
+                    }
+                } else {
+                    // more than the list holds: find them again, with the
+                    // same arithmetic as pair_images, lane by lane
+                    for (int jj = j_lo; jj < j_lo + jlen; ++jj) {
+                        const Part<R> &pb = tj[c * 32 + jj];
+                        const PairGeom<R, DIM> g = pair_geom<R, DIM>(s, pi, pb);
+                        const int c0 = ims.cand[g.sc * s.cand_max];
+                        const R r2 = image_r2<DIM>(g.x, ims.img[c0]);
+                        const bool pass = r2 < (valid(jj) ? FP<R>::rc2(s) : R(0));
+                        if (is_close_primary<R, DIM>(s, c0, r2, pass))
+                            acc.add64(close_pair_term<DIM>(s, pi, pb, (double)(R(1) * pi.q * pb.q), b.status));
+                    }
+                }
+                __syncwarp();
+            }
+        }
         const double v = warp_sum(acc.get());
         if (lane == 0) red[u] = v;
     }

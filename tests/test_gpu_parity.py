@@ -72,6 +72,21 @@ def small_case(name, W):
         d["pos"] = I.uniform_positions(rng, lat, W, 1)
         d["q"] = np.array([-1.0])
         d["fixed_pos"], d["fixed_q"] = np.zeros((0, 3)), np.zeros(0)
+    elif name == "clustered":
+        # half the electrons in a ball of radius 0.25 of the mean spacing:
+        # hundreds of close pairs per 32 x 32 sub-tile, more than the FP32
+        # path's deferred close-pair list holds, so its rescan runs
+        lat = I.sc_lattice(80, 1.5)
+        spacing = abs(np.linalg.det(lat)) ** (1 / 3) / 80 ** (1 / 3)
+        d = dict(dim=3, lattice=lat, n=80, alpha=5.0 / lat[0, 0])
+        pos = I.uniform_positions(rng, lat, W, 80)
+        for k in range(W):
+            v = rng.normal(size=(40, 3))
+            v *= (0.25 * spacing * rng.random((40, 1)) ** (1 / 3)) / np.linalg.norm(v, axis=1, keepdims=True)
+            pos[k, :40] = pos[k, 0] + v
+        d["pos"] = pos
+        d["q"] = -np.ones(80)
+        d["fixed_pos"], d["fixed_q"] = np.zeros((0, 3)), np.zeros(0)
     elif name == "mixed_q":
         lat = I.sc_lattice(40, 1.2)
         d = dict(dim=3, lattice=lat, n=40, alpha=5.0 / lat[0, 0])
@@ -91,7 +106,7 @@ def make(ew, w, prec, **kw):
     return ctx, b
 
 
-CASES = ["sc54", "fcc100", "hex70", "diamond1", "single", "mixed_q"]
+CASES = ["sc54", "fcc100", "hex70", "diamond1", "single", "mixed_q", "clustered"]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
