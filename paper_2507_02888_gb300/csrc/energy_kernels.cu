@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kSfacThreads)
 // -------------------------------------------------------------- real space
 // Persistent CTAs walk the (walker, tile pair) items; see real_item.
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kRealThreads, kRealMinBlocks) k_real(SysDev s, BatchDev b) {
+__global__ void __launch_bounds__(kRealThreads, sizeof(R) == 4 ? kRealMinBlocks32 : kRealMinBlocks64) k_real(SysDev s, BatchDev b) {
     extern __shared__ __align__(32) unsigned char smem[];
     ImageSmem<R> ims;
     ims.carve(smem, s, DIM);

@@ -24,7 +24,8 @@ namespace ewald {
 
 constexpr int kRealWarps = 4;          // warps per real-space CTA
 constexpr int kRealThreads = 32 * kRealWarps;
-constexpr int kRealMinBlocks = 10;     // resident real-space CTAs per SM the registers are sized for
+// resident real-space CTAs per SM the registers are sized for (FP32, FP64 path)
+constexpr int kRealMinBlocks32 = 10, kRealMinBlocks64 = 8;
 constexpr int kQueueCap = 96;          // per-warp queue of accepted (r^2, weight) terms
 constexpr int kSfacThreads = 256;      // threads (= runs) per structure-factor CTA
 constexpr int kMoveThreads = 256;      // threads per walker in propose / accept
