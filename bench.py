@@ -158,6 +158,7 @@ def source_hash(files):
 
 
 REAL_SOURCES = ["paper_2507_02888_gb300/csrc/energy_kernels.cu", "paper_2507_02888_gb300/csrc/energy_items.cuh",
+                "paper_2507_02888_gb300/csrc/ewald_internal.h",
                 "paper_2507_02888_gb300/csrc/device_common.cuh"]
 
 

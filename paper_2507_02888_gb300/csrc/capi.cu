@@ -118,7 +118,10 @@ int build_device(ewald_ctx *c) {
     s.n_runs = (int)t.runs.size() / 4;
     s.run_len = t.run_len;
     s.n_gh = (int)t.g2slot.size();
-    s.n_gchunks = (s.n_runs + kSfacThreads - 1) / kSfacThreads;
+    // as few chunks as kSfacThreads allows, split evenly (whole warps)
+    const int n_ch = (s.n_runs + kSfacThreads - 1) / kSfacThreads;
+    s.sfac_threads = ((s.n_runs + n_ch - 1) / n_ch + 31) / 32 * 32;
+    s.n_gchunks = (s.n_runs + s.sfac_threads - 1) / s.sfac_threads;
     s.n1max = std::max(t.n1max, 1);
     s.n2max = std::max(t.n2max, 1);
     s.n3max = std::max(t.n3max, 1);
@@ -721,7 +724,7 @@ namespace {
 // one electron-G term = 1; a pair costs its candidate tests and its terms).
 double item_cost(const SysDev &s, int kind, int sub) {
     if (kind == kItemSfac) {
-        int runs = std::min(kSfacThreads, s.n_runs - sub * kSfacThreads);  // run lengths vary; bound
+        int runs = std::min(s.sfac_threads, s.n_runs - sub * s.sfac_threads);  // run lengths vary; bound
         return (double)runs * s.run_len * s.n_mob;
     }
     return 1.0;  // scaled by the caller

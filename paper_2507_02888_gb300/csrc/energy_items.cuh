@@ -27,8 +27,40 @@ __host__ __device__ inline size_t real_work_bytes(const SysDev &s, int precision
            align16((size_t)warps * kCloseCap * sizeof(unsigned)) + align16(kRealUnits * sizeof(double));
 }
 
-// One CTA; blockDim.x threads, each owning one run of <= kRunLen consecutive
-// n1 in a row (n2, n3), walked away from the row's smallest |G|.  Electrons are staged in tiles of te; for each
+// Tables of one electron tile in shared memory (see sfac_item).
+template <typename R>
+struct SfacTile {
+    const Part<R> *tp;
+    const Cx<R> *P1, *P2, *P3;
+    int W1, W2, W3, n1max, n2max, ne;
+};
+
+// One thread's run over the tile's electrons: the run's first G from three
+// buffered powers, then one complex multiplication per G along n1.  L is the
+// longest run of the warp (compile-time, so the accumulators stay in
+// registers and the warp does no steps past its longest run).
+template <typename R, int DIM, int L>
+__device__ __forceinline__ void sfac_runs(const SfacTile<R> &t, int4 rn, int dir, R *tx, R *ty) {
+    using C = Cx<R>;
+    for (int e = 0; e < t.ne; ++e) {
+        const R q = t.tp[e].q;
+        C z = cmul(t.P1[(size_t)e * t.W1 + rn.x + t.n1max], t.P2[(size_t)e * t.W2 + rn.y + t.n2max]);
+        if (DIM == 3) z = cmul(z, t.P3[(size_t)e * t.W3 + rn.z]);
+        const C step = t.P1[(size_t)e * t.W1 + t.n1max + dir];
+#pragma unroll
+        for (int r = 0; r < L; ++r) {
+            if (r < rn.w) {
+                tx[r] += q * z.x;
+                ty[r] += q * z.y;
+                if (r + 1 < L) z = cmul(z, step);
+            }
+        }
+    }
+}
+
+// One CTA; the first s.sfac_threads threads each own one run of <= kRunLen
+// consecutive n1 in a row (n2, n3), walked away from the row's smallest |G|
+// (chunk c holds runs c * sfac_threads ...; other threads only help stage).  Electrons are staged in tiles of te; for each
 // electron of the tile the CTA buffers the powers e^{2 pi i n f_k},
 // n = -n_max..n_max, built by repeated multiplication from the base phase.
 // A thread starts its run from the product of three buffered powers and
@@ -46,11 +78,13 @@ __device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, 
     double *red = (double *)(smem + align16(te * sizeof(Part<R>)) + align16((size_t)te * (W1 + W2 + W3) * sizeof(C)));
 
     const int tid = threadIdx.x;
-    const int run = chunk * blockDim.x + tid;
-    const bool has = run < s.n_runs;
+    const int run = chunk * s.sfac_threads + tid;
+    const bool has = tid < s.sfac_threads && run < s.n_runs;
     const int4 rn0 = has ? s.runs[run] : make_int4(0, 0, 0, 0);
     const int dir = rn0.w < 0 ? -1 : 1;             // the run walks n1 = start + dir * r
     const int4 rn = make_int4(rn0.x, rn0.y, rn0.z, rn0.w * dir);
+    // runs are stored longest first, so lane 0 holds the warp's longest run
+    const int wmax = __shfl_sync(0xffffffffu, rn.w, 0);
     double ax[kRunLen], ay[kRunLen];
 #pragma unroll
     for (int r = 0; r < kRunLen; ++r) ax[r] = ay[r] = 0;
@@ -88,21 +122,17 @@ __device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, 
         R tx[kRunLen], ty[kRunLen];
 #pragma unroll
         for (int r = 0; r < kRunLen; ++r) tx[r] = ty[r] = 0;
-        if (has) {
-            for (int e = 0; e < ne; ++e) {
-                const R q = tp[e].q;
-                C z = cmul(P1[(size_t)e * W1 + rn.x + s.n1max], P2[(size_t)e * W2 + rn.y + s.n2max]);
-                if (DIM == 3) z = cmul(z, P3[(size_t)e * W3 + rn.z]);
-                const C step = P1[(size_t)e * W1 + s.n1max + dir];
-#pragma unroll
-                for (int r = 0; r < kRunLen; ++r) {
-                    if (r < rn.w) {
-                        tx[r] += q * z.x;
-                        ty[r] += q * z.y;
-                        z = cmul(z, step);
-                    }
-                }
-            }
+        const SfacTile<R> tl{tp, P1, P2, P3, W1, W2, W3, s.n1max, s.n2max, ne};
+        switch (wmax) {  // uniform over the warp: the loop stops at the warp's longest run
+            case 8: sfac_runs<R, DIM, 8>(tl, rn, dir, tx, ty); break;
+            case 7: sfac_runs<R, DIM, 7>(tl, rn, dir, tx, ty); break;
+            case 6: sfac_runs<R, DIM, 6>(tl, rn, dir, tx, ty); break;
+            case 5: sfac_runs<R, DIM, 5>(tl, rn, dir, tx, ty); break;
+            case 4: sfac_runs<R, DIM, 4>(tl, rn, dir, tx, ty); break;
+            case 3: sfac_runs<R, DIM, 3>(tl, rn, dir, tx, ty); break;
+            case 2: sfac_runs<R, DIM, 2>(tl, rn, dir, tx, ty); break;
+            case 1: sfac_runs<R, DIM, 1>(tl, rn, dir, tx, ty); break;
+            default: break;
         }
 #pragma unroll
         for (int r = 0; r < kRunLen; ++r) {

@@ -61,7 +61,8 @@ __global__ void k_positions_out(SysDev s, BatchDev b, double *__restrict__ pos) 
 }
 
 // ------------------------------------------------------- structure factor
-// One CTA per (walker, chunk of kSfacThreads G runs); see sfac_item.  With
+// One CTA of s.sfac_threads threads per (walker, chunk of that many G runs);
+// see sfac_item.  With
 // `only`, walkers whose flag is 0 are skipped (re-sum after accepted moves).
 template <typename R, int DIM>
 __global__ void __launch_bounds__(kSfacThreads)
@@ -182,11 +183,11 @@ int launch_sfac(const SysDev &s, const BatchDev &b, int precision, const LaunchC
     int grid = b.W * s.n_gchunks;
     int we = only ? 0 : 1;
     if (precision == EWALD_FP64) {
-        if (s.dim == 3) k_sfac<double, 3><<<grid, kSfacThreads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
-        else k_sfac<double, 2><<<grid, kSfacThreads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
+        if (s.dim == 3) k_sfac<double, 3><<<grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
+        else k_sfac<double, 2><<<grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
     } else {
-        if (s.dim == 3) k_sfac<float, 3><<<grid, kSfacThreads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
-        else k_sfac<float, 2><<<grid, kSfacThreads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
+        if (s.dim == 3) k_sfac<float, 3><<<grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
+        else k_sfac<float, 2><<<grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
     }
     return cudaGetLastError();
 }

@@ -64,6 +64,7 @@ struct SysDev {
     const int2 *items;               // (ti, tj); tj >= n_mob_tiles -> fixed tile tj - n_mob_tiles
     // reciprocal space
     int n_runs, run_len, n_gh, n_gchunks, sfac_te;
+    int sfac_threads;  // runs per structure-factor chunk (multiple of 32, <= kSfacThreads)
     int n1max, n2max, n3max;
     const int4 *runs;  // (n1 start, n2, n3, dir * length), dir = +-1
     const double *gw_d;

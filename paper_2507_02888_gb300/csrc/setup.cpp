@@ -272,6 +272,20 @@ static void build_gvectors(HostTables *t) {
         t->n2max = std::max(t->n2max, std::abs(r.n2));
         t->n3max = std::max(t->n3max, std::abs(r.n3));
     }
+    // Longest runs first (stable): the structure-factor kernel's warps then
+    // hold runs of nearly one length and stop at their own longest.
+    {
+        const int nr = (int)t->runs.size() / 4;
+        std::vector<int> order(nr);
+        for (int i = 0; i < nr; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return std::abs(t->runs[4 * a + 3]) > std::abs(t->runs[4 * b + 3]);
+        });
+        std::vector<int> sorted;
+        sorted.reserve(t->runs.size());
+        for (int i : order) sorted.insert(sorted.end(), t->runs.begin() + 4 * i, t->runs.begin() + 4 * i + 4);
+        t->runs.swap(sorted);
+    }
     int n_runs = (int)t->runs.size() / 4;
     int slots = n_runs * t->run_len;
     t->gw.assign(slots, 0.0);
