@@ -96,9 +96,8 @@ int build_device(ewald_ctx *c) {
     double L = std::pow(t.volume, 1.0 / dim);
     s.coin2 = 1e-20 * L * L;
     s.coin2_f = (float)s.coin2;
-    // close radius: 0.3 of the mean spacing of all charges
-    const double spacing = std::pow(t.volume / (double)(t.n_mob + t.n_fix), 1.0 / dim);
-    s.close2_f = (float)(0.09 * spacing * spacing);
+    // close radius of the FP32 path (set-up: r_close)
+    s.close2_f = (float)(t.r_close * t.r_close);
     cudaError_t e;
     // images
     int n_img = (int)t.img.size() / 3;
@@ -363,7 +362,7 @@ bool tiling_allowed(const ewald_ctx *c, int S, int bits) {
     const HostTables &t = c->t;
     if (32 * S > std::max(32, 2 * t.n_mob)) return false;
     int max_bits = t.dim == 3 ? 4 : 6;
-    return bits >= 0 && bits <= max_bits && subcell_bytes(t, bits) <= 48 * 1024;
+    return bits >= t.min_bits && bits <= max_bits && subcell_bytes(t, bits) <= 48 * 1024;
 }
 
 bool ready(ewald_batch *b) {

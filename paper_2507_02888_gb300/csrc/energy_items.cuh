@@ -35,24 +35,70 @@ struct SfacTile {
     int W1, W2, W3, n1max, n2max, ne;
 };
 
+// Sum of one G slot over all electrons.  FP64: plain.  FP32: Kahan
+// compensated, term by term (the FP32 form's compensated accumulation per G);
+// converted to FP64 once, when rho(G) is stored.
+template <typename R>
+struct SlotSum;
+template <>
+struct SlotSum<double> {
+    double s = 0;
+    __device__ void add(double t) { s += t; }
+    __device__ double get() const { return s; }
+};
+template <>
+struct SlotSum<float> {
+    float s = 0, c = 0;
+    __device__ void add(float t) {
+        const float y = t - c, u = s + y;
+        c = (u - s) - y;
+        s = u;
+    }
+    __device__ double get() const { return (double)s - (double)c; }
+};
+
 // One thread's run over the tile's electrons: the run's first G from three
-// buffered powers, then one complex multiplication per G along n1.  L is the
-// longest run of the warp (compile-time, so the accumulators stay in
+// buffered powers, then one complex multiplication per G along n1.  Two
+// electrons are walked side by side, so two independent multiplication
+// chains are in flight, and their two terms enter the slot sums together.
+// L is the longest run of the warp (compile-time, so the sums stay in
 // registers and the warp does no steps past its longest run).
 template <typename R, int DIM, int L>
-__device__ __forceinline__ void sfac_runs(const SfacTile<R> &t, int4 rn, int dir, R *tx, R *ty) {
+__device__ __forceinline__ void sfac_runs(const SfacTile<R> &t, int4 rn, int dir, SlotSum<R> *ax, SlotSum<R> *ay) {
     using C = Cx<R>;
-    for (int e = 0; e < t.ne; ++e) {
-        const R q = t.tp[e].q;
-        C z = cmul(t.P1[(size_t)e * t.W1 + rn.x + t.n1max], t.P2[(size_t)e * t.W2 + rn.y + t.n2max]);
+    auto start = [&](int e, C &z, C &step) {
+        z = cmul(t.P1[(size_t)e * t.W1 + rn.x + t.n1max], t.P2[(size_t)e * t.W2 + rn.y + t.n2max]);
         if (DIM == 3) z = cmul(z, t.P3[(size_t)e * t.W3 + rn.z]);
-        const C step = t.P1[(size_t)e * t.W1 + t.n1max + dir];
+        step = t.P1[(size_t)e * t.W1 + t.n1max + dir];
+    };
+    int e = 0;
+    for (; e + 1 < t.ne; e += 2) {
+        const R qa = t.tp[e].q, qb = t.tp[e + 1].q;
+        C za, sa, zb, sb;
+        start(e, za, sa);
+        start(e + 1, zb, sb);
 #pragma unroll
         for (int r = 0; r < L; ++r) {
             if (r < rn.w) {
-                tx[r] += q * z.x;
-                ty[r] += q * z.y;
-                if (r + 1 < L) z = cmul(z, step);
+                ax[r].add(qa * za.x + qb * zb.x);
+                ay[r].add(qa * za.y + qb * zb.y);
+                if (r + 1 < L) {
+                    za = cmul(za, sa);
+                    zb = cmul(zb, sb);
+                }
+            }
+        }
+    }
+    if (e < t.ne) {
+        const R q = t.tp[e].q;
+        C z, st;
+        start(e, z, st);
+#pragma unroll
+        for (int r = 0; r < L; ++r) {
+            if (r < rn.w) {
+                ax[r].add(q * z.x);
+                ay[r].add(q * z.y);
+                if (r + 1 < L) z = cmul(z, st);
             }
         }
     }
@@ -85,15 +131,14 @@ __device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, 
     const int4 rn = make_int4(rn0.x, rn0.y, rn0.z, rn0.w * dir);
     // runs are stored longest first, so lane 0 holds the warp's longest run
     const int wmax = __shfl_sync(0xffffffffu, rn.w, 0);
-    double ax[kRunLen], ay[kRunLen];
-#pragma unroll
-    for (int r = 0; r < kRunLen; ++r) ax[r] = ay[r] = 0;
+    SlotSum<R> ax[kRunLen], ay[kRunLen];
 
     for (int e0 = 0; e0 < s.n_mob; e0 += te) {
         const int ne = min(te, s.n_mob - e0);
         __syncthreads();  // the previous tile's tables are no longer read
         for (int t = tid; t < ne; t += blockDim.x) tp[t] = load_mobile<R>(s, b, w, e0 + t, DIM);
         __syncthreads();
+        // powers by repeated multiplication (Eq. (10))
         for (int t = tid; t < ne * DIM; t += blockDim.x) {
             const int e = t / DIM, k = t - e * DIM;
             R sn, cs;
@@ -119,25 +164,17 @@ __device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, 
             }
         }
         __syncthreads();
-        R tx[kRunLen], ty[kRunLen];
-#pragma unroll
-        for (int r = 0; r < kRunLen; ++r) tx[r] = ty[r] = 0;
         const SfacTile<R> tl{tp, P1, P2, P3, W1, W2, W3, s.n1max, s.n2max, ne};
         switch (wmax) {  // uniform over the warp: the loop stops at the warp's longest run
-            case 8: sfac_runs<R, DIM, 8>(tl, rn, dir, tx, ty); break;
-            case 7: sfac_runs<R, DIM, 7>(tl, rn, dir, tx, ty); break;
-            case 6: sfac_runs<R, DIM, 6>(tl, rn, dir, tx, ty); break;
-            case 5: sfac_runs<R, DIM, 5>(tl, rn, dir, tx, ty); break;
-            case 4: sfac_runs<R, DIM, 4>(tl, rn, dir, tx, ty); break;
-            case 3: sfac_runs<R, DIM, 3>(tl, rn, dir, tx, ty); break;
-            case 2: sfac_runs<R, DIM, 2>(tl, rn, dir, tx, ty); break;
-            case 1: sfac_runs<R, DIM, 1>(tl, rn, dir, tx, ty); break;
+            case 8: sfac_runs<R, DIM, 8>(tl, rn, dir, ax, ay); break;
+            case 7: sfac_runs<R, DIM, 7>(tl, rn, dir, ax, ay); break;
+            case 6: sfac_runs<R, DIM, 6>(tl, rn, dir, ax, ay); break;
+            case 5: sfac_runs<R, DIM, 5>(tl, rn, dir, ax, ay); break;
+            case 4: sfac_runs<R, DIM, 4>(tl, rn, dir, ax, ay); break;
+            case 3: sfac_runs<R, DIM, 3>(tl, rn, dir, ax, ay); break;
+            case 2: sfac_runs<R, DIM, 2>(tl, rn, dir, ax, ay); break;
+            case 1: sfac_runs<R, DIM, 1>(tl, rn, dir, ax, ay); break;
             default: break;
-        }
-#pragma unroll
-        for (int r = 0; r < kRunLen; ++r) {
-            ax[r] += (double)tx[r];
-            ay[r] += (double)ty[r];
         }
     }
 
@@ -151,8 +188,8 @@ __device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, 
                 const int slot = r * s.n_runs + run;
                 double2 v = make_double2(0.0, 0.0);
                 if (r < rn.w) {
-                    v.x = ax[r];
-                    v.y = ay[r];
+                    v.x = ax[r].get();
+                    v.y = ay[r].get();
                     if (s.rho_fix) {
                         v.x += s.rho_fix[slot].x;
                         v.y += s.rho_fix[slot].y;
@@ -245,7 +282,8 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
                     for (int e = lane; e < cl.n; e += 32) {
                         const unsigned id = cl.e[e];
                         const Part<R> &pa = ti[id >> 16], &pb = tj[id & 0xffffu];
-                        acc.add64(close_pair_term<DIM>(s, pa, pb, (double)(R(1) * pa.q * pb.q), b.status));
+                        const int c0 = ims.cand[pair_geom<R, DIM>(s, pa, pb).sc * s.cand_max];
+                        acc.add64(close_pair_term<DIM>(s, pa, pb, c0, (double)(R(1) * pa.q * pb.q), b.status));
                     }
                 } else {
                     // more than the list holds: find them again, with the
@@ -256,8 +294,8 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
                         const int c0 = ims.cand[g.sc * s.cand_max];
                         const R r2 = image_r2<DIM>(g.x, ims.img[c0]);
                         const bool pass = r2 < (valid(jj) ? FP<R>::rc2(s) : R(0));
-                        if (is_close_primary<R, DIM>(s, c0, r2, pass))
-                            acc.add64(close_pair_term<DIM>(s, pi, pb, (double)(R(1) * pi.q * pb.q), b.status));
+                        if (is_close_first<R, DIM>(s, r2, pass))
+                            acc.add64(close_pair_term<DIM>(s, pi, pb, c0, (double)(R(1) * pi.q * pb.q), b.status));
                     }
                 }
                 __syncwarp();

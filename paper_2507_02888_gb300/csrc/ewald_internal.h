@@ -27,7 +27,8 @@ constexpr int kRealThreads = 32 * kRealWarps;
 // resident real-space CTAs per SM the registers are sized for (FP32, FP64 path)
 constexpr int kRealMinBlocks32 = 10, kRealMinBlocks64 = 8;
 constexpr int kQueueCap = 96;          // per-warp queue of accepted (r^2, weight) terms
-constexpr int kSfacThreads = 256;      // threads (= runs) per structure-factor CTA
+constexpr int kSfacThreads = 256;      // threads (= runs) per structure-factor CTA, at most
+constexpr int kSfacMinBlocks = 3;      // resident structure-factor CTAs per SM the registers are sized for
 constexpr int kMoveThreads = 256;      // threads per walker in propose / accept
 constexpr int kRunLen = 8;             // maximum G run length (compile-time)
 // default real-space cutoff of the mixed path: erfc(alpha r_c) = kMixedRealTol
@@ -103,6 +104,8 @@ struct HostTables {
     // real space
     std::vector<double> img;   // [n_img][3]
     int sub_bits = 0, cand_max = 0;
+    int min_bits = 0;      // coarsest displacement cells for which candidate 0 covers r_close
+    double r_close = 0;    // FP32 path: pairs closer than this (any image) go to FP64
     std::vector<unsigned short> cand;  // [n_sub][cand_max]
     std::vector<int> cand_len;         // [n_sub]
     // reciprocal space

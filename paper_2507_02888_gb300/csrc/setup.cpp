@@ -128,6 +128,36 @@ static double max_wrapped_norm(const HostTables &t) {
     return best;
 }
 
+// Close radius of the FP32 path and the coarsest displacement cells that go
+// with it.  A displacement within r_close of an image R (a physically close
+// pair, possibly across the cell boundary) has its term evaluated in FP64.
+// The FP32 loop tests only candidate 0 of each cell for this, which is
+// enough when no two images can come within r_close of one cell: two such
+// images are less than 2 (r_close + cell radius) apart, so it suffices that
+// 2 (r_close + max_wrapped_norm / 2^bits) < |R_min|.  r_close = 0.3 of the
+// mean spacing of all charges, lowered if the cell is very flat.
+static void set_close_radius(HostTables *t) {
+    const int dim = t->dim;
+    double rmin = 1e300;
+    for (int m0 = -2; m0 <= 2; ++m0)
+        for (int m1 = -2; m1 <= 2; ++m1)
+            for (int m2 = (dim == 3 ? -2 : 0); m2 <= (dim == 3 ? 2 : 0); ++m2) {
+                if (!m0 && !m1 && !m2) continue;
+                double m[3] = {(double)m0, (double)m1, (double)m2}, x[3];
+                lat_to_cart(*t, m, x);
+                rmin = std::min(rmin, norm_n(x, dim));
+            }
+    const double spacing = std::pow(t->volume / (double)(t->n_mob + t->n_fix), 1.0 / dim);
+    double rc = std::min(0.3 * spacing, 0.25 * rmin);
+    const double wn = max_wrapped_norm(*t);
+    const int max_bits = dim == 3 ? 4 : 6;
+    int b = 0;
+    while (b < max_bits && 2 * (rc + wn / (1 << b)) >= rmin) ++b;
+    rc = std::min(rc, 0.999 * (0.5 * rmin - wn / (1 << b)));
+    t->r_close = std::max(rc, 0.0);
+    t->min_bits = b;
+}
+
 static void build_images(HostTables *t) {
     int dim = t->dim;
     double reach = t->r_c + max_wrapped_norm(*t);
@@ -148,8 +178,9 @@ static void build_images(HostTables *t) {
     for (auto &i : v) t->img.insert(t->img.end(), {i.x[0], i.x[1], i.x[2]});
 }
 
-// Candidate lists for 2^bits displacement cells per axis.  Returns the
-// longest list.  A displacement cell is the parallelepiped [-1/2 + s/M,
+// Candidate lists for 2^bits displacement cells per axis, in image-table
+// order except that the image nearest to the cell's centre comes first.
+// Returns the longest list.  A displacement cell is the parallelepiped [-1/2 + s/M,
 // -1/2 + (s+1)/M) of fractional coordinates; every point in it is within
 // d_max / M of its centre, so R can contribute only if |c + R| < r_c + d_max/M.
 static int build_cand(const HostTables &t, int bits, std::vector<unsigned short> *cand,
@@ -165,11 +196,21 @@ static int build_cand(const HostTables &t, int bits, std::vector<unsigned short>
         double f[3] = {0, 0, 0}, c[3];
         for (int k = 0; k < dim; ++k) f[k] = -0.5 + (((s >> (k * bits)) & (M - 1)) + 0.5) / M;
         lat_to_cart(t, f, c);
+        int nearest = -1;
+        double dn = 1e300;
         for (int i = 0; i < n_img; ++i) {
             double x[3];
             for (int y = 0; y < 3; ++y) x[y] = c[y] + t.img[3 * i + y];
-            if (norm_n(x, dim) < lim) lists[s].push_back((unsigned short)i);
+            const double r = norm_n(x, dim);
+            if (r < lim) {
+                if (r < dn) dn = r, nearest = (int)lists[s].size();
+                lists[s].push_back((unsigned short)i);
+            }
         }
+        // the image nearest to the cell's centre first: with at least
+        // min_bits bits it is the only one that can bring a displacement of
+        // the cell within r_close (see set_close_radius)
+        if (nearest > 0) std::rotate(lists[s].begin(), lists[s].begin() + nearest, lists[s].begin() + nearest + 1);
         longest = std::max(longest, (int)lists[s].size());
     }
     if (cand) {
@@ -199,13 +240,13 @@ size_t subcell_bytes(const HostTables &t, int bits) {
 // Choose the number of displacement cells: the shortest longest-list whose
 // table fits in max_bytes of shared memory.
 int pick_subcells(HostTables *t, int max_bytes) {
-    int best_bits = 0, best_len = 1 << 30;
+    int best_bits = t->min_bits, best_len = 1 << 30;
     int max_bits = t->dim == 3 ? 4 : 6;
-    for (int b = 0; b <= max_bits; ++b) {
+    for (int b = t->min_bits; b <= max_bits; ++b) {
         int n_sub = 1 << (b * t->dim);
         int L = build_cand(*t, b, nullptr, nullptr);
         size_t bytes = (size_t)n_sub * L * 2 + (size_t)n_sub * 4;
-        if (bytes > (size_t)max_bytes) break;
+        if (bytes > (size_t)max_bytes && b > t->min_bits) break;
         if (L < best_len) {
             best_len = L;
             best_bits = b;
@@ -441,6 +482,7 @@ int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
         *why = "real-space cutoff needs more than 4000 candidate images";
         return EWALD_ERR_ARG;
     }
+    set_close_radius(t);
     pick_subcells(t, 24 * 1024);
     build_gvectors(t);
     if (t->runs.empty()) {
