@@ -65,7 +65,7 @@ __global__ void k_positions_out(SysDev s, BatchDev b, double *__restrict__ pos) 
 // see sfac_item.  With
 // `only`, walkers whose flag is 0 are skipped (re-sum after accepted moves).
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kSfacThreads, kSfacMinBlocks)
+__global__ void __launch_bounds__(kSfacThreads, sizeof(R) == 4 ? kSfacMinBlocks32 : kSfacMinBlocks64)
     k_sfac(SysDev s, BatchDev b, const unsigned char *__restrict__ only, int te, int write_energy) {
     extern __shared__ __align__(32) unsigned char smem[];
     const int w = blockIdx.x / s.n_gchunks, chunk = blockIdx.x - w * s.n_gchunks;

@@ -28,7 +28,8 @@ constexpr int kRealThreads = 32 * kRealWarps;
 constexpr int kRealMinBlocks32 = 10, kRealMinBlocks64 = 8;
 constexpr int kQueueCap = 96;          // per-warp queue of accepted (r^2, weight) terms
 constexpr int kSfacThreads = 256;      // threads (= runs) per structure-factor CTA, at most
-constexpr int kSfacMinBlocks = 3;      // resident structure-factor CTAs per SM the registers are sized for
+// resident structure-factor CTAs per SM the registers are sized for (FP32, FP64 path)
+constexpr int kSfacMinBlocks32 = 3, kSfacMinBlocks64 = 2;
 constexpr int kMoveThreads = 256;      // threads per walker in propose / accept
 constexpr int kRunLen = 8;             // maximum G run length (compile-time)
 // default real-space cutoff of the mixed path: erfc(alpha r_c) = kMixedRealTol
