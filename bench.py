@@ -173,6 +173,17 @@ def profiled_traffic(workload, precision):
     return d.get("dram_bytes_per_launch")
 
 
+def ranks_max(vals, world):
+    """Element-wise maximum of per-rank timings over all ranks (host tensors:
+    the process group is gloo, used for the barrier and this maximum only)."""
+    if world == 1:
+        return list(vals)
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
 def expected_real_terms(info, w):
     """Mean number of real-space terms per walker for uniform random displacements.
 
@@ -245,11 +256,7 @@ def run_ours(args, rank, world, local_rank):
         return t_e, t_m, ctx.timing(), clk
 
     def max_over_ranks(vals):
-        if world == 1:
-            return vals
-        t = torch.tensor(vals, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return t.tolist()
+        return ranks_max(vals, world)
 
     # ---- mixed precision, batched: the headline
     ctx, b = make("mixed")
