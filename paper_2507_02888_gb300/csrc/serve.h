@@ -6,6 +6,8 @@
 
 namespace ewald {
 
+constexpr int kServeMinBlocks = 3;  // resident serving CTAs per SM the registers are sized for
+
 // One active request: its walkers' state and its move stream.
 struct SlotDev {
     BatchDev b;               // positions, rho(G), running energies e[W], acc_count

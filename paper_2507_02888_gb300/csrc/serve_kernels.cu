@@ -33,13 +33,14 @@ __device__ inline void cta_copy_words(T *dst, const T *src) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kMoveThreads) k_serve_step(ServeDev sv) {
+__global__ void __launch_bounds__(kMoveThreads, kServeMinBlocks) k_serve_step(ServeDev sv) {
     extern __shared__ __align__(32) unsigned char smem[];
     __shared__ SysDev ss;
     __shared__ SlotDev sl;
-    __shared__ int s_item, s_img_sys, s_k, s_acc, s_resum;
-    __shared__ unsigned long long s_uold[3], s_unew[3];
-    if (threadIdx.x == 0) s_img_sys = -1;
+    __shared__ int s_item, s_img_sys, s_slot, s_k, s_acc, s_resum;
+    __shared__ unsigned long long s_uold[3], s_unew[3], s_x[6];
+    __shared__ double s_g[4];
+    if (threadIdx.x == 0) s_img_sys = s_slot = -1;
     const int n_items = *sv.n_items;
     for (;;) {
         __syncthreads();
@@ -48,10 +49,13 @@ __global__ void __launch_bounds__(kMoveThreads) k_serve_step(ServeDev sv) {
         const int it = s_item;
         if (it >= n_items) break;
         const int2 d = sv.items[it];  // (slot, walker)
-        cta_copy_words(&sl, sv.slots + d.x);
-        __syncthreads();
-        cta_copy_words(&ss, sv.sys + sl.sys);
-        __syncthreads();
+        if (d.x != s_slot) {          // uniform over the CTA; items come slot by slot
+            cta_copy_words(&sl, sv.slots + d.x);
+            __syncthreads();
+            cta_copy_words(&ss, sv.sys + sl.sys);
+            __syncthreads();
+            if (threadIdx.x == 0) s_slot = d.x;
+        }
         const int w = d.y, dim = ss.dim;
         MoveSmem<R> m;
         m.carve_split(smem, smem + sv.img_bytes, ss, dim);
@@ -60,21 +64,24 @@ __global__ void __launch_bounds__(kMoveThreads) k_serve_step(ServeDev sv) {
             __syncthreads();
             if (threadIdx.x == 0) s_img_sys = sl.sys;
         }
+        // the walker's six draws of this step, one per thread, then the two
+        // Box-Muller pairs on two threads
+        const unsigned long long c0 = (((unsigned long long)sl.step << 32) + (unsigned long long)w) * 8ull;
+        if (threadIdx.x < 6) s_x[threadIdx.x] = splitmix_out(sl.seed, c0 + threadIdx.x);
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int p = threadIdx.x;
+            const double u1 = uniform53(s_x[1 + 2 * p]), u2 = uniform53(s_x[2 + 2 * p]);
+            const double rad = sqrt(-2.0 * log(1.0 - u1));
+            double sn, cs;
+            sincospi(2.0 * u2, &sn, &cs);
+            s_g[2 * p] = rad * cs;
+            s_g[2 * p + 1] = rad * sn;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            const unsigned long long c0 = (((unsigned long long)sl.step << 32) + (unsigned long long)w) * 8ull;
-            const unsigned long long x0 = splitmix_out(sl.seed, c0);
-            const int k = (int)(((x0 >> 32) * (unsigned long long)ss.n_mob) >> 32);
-            double g[4];
-            for (int p = 0; p < 2; ++p) {
-                const double u1 = uniform53(splitmix_out(sl.seed, c0 + 1 + 2 * p));
-                const double u2 = uniform53(splitmix_out(sl.seed, c0 + 2 + 2 * p));
-                const double rad = sqrt(-2.0 * log(1.0 - u1));
-                double sn, cs;
-                sincospi(2.0 * u2, &sn, &cs);
-                g[2 * p] = rad * cs;
-                g[2 * p + 1] = rad * sn;
-            }
-            const double ua = uniform53(splitmix_out(sl.seed, c0 + 5));
+            const int k = (int)(((s_x[0] >> 32) * (unsigned long long)ss.n_mob) >> 32);
+            const double ua = uniform53(s_x[5]);
             // current Cartesian position of particle k, displaced
             double f[3] = {0, 0, 0}, r[3] = {0, 0, 0};
             for (int q = 0; q < dim; ++q) {
@@ -83,7 +90,7 @@ __global__ void __launch_bounds__(kMoveThreads) k_serve_step(ServeDev sv) {
             }
             for (int x = 0; x < dim; ++x) {
                 for (int q = 0; q < dim; ++q) r[x] += f[q] * ss.A[q][x];
-                r[x] += sl.sigma * g[x];
+                r[x] += sl.sigma * s_g[x];
             }
             unsigned long long un[3] = {0, 0, 0};
             for (int q = 0; q < dim; ++q) {
