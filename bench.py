@@ -173,6 +173,34 @@ def profiled_traffic(workload, precision):
     return d.get("dram_bytes_per_launch")
 
 
+def measured_hbm():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "of measured (MEASURED_PEAKS.json copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback (6.8 TB/s)"
+
+
+def move_roofline(info, w, W, moves_per_s, accept_frac, peaks, hbm_peak, hbm_basis):
+    """Algorithmic bytes and flops of one propose + accept of one walker, and
+    the fractions of HBM bandwidth and FP32 FMA rate they reach."""
+    if not moves_per_s:
+        return None
+    n, nf, dim, ngh = w["n"], len(w["fixed_q"]), w["dim"], info["n_g_half"]
+    # propose: rho(G) of the walker and every particle's position; accept:
+    # rho(G) read-modify-write and the moved position, for accepted moves
+    bytes_move = ngh * 16 + (n + nf) * dim * 8 + accept_frac * (2 * ngh * 16 + dim * 8)
+    dim_ball = 4.0 / 3.0 * math.pi * info["r_cutoff"] ** 3 if dim == 3 else math.pi * info["r_cutoff"] ** 2
+    terms = 2 * (n - 1 + nf) * dim_ball / info["volume"]      # old and new position against all others
+    flop_move = terms * FLOP_REAL_TERM + 2 * ngh * FLOP_G_TERM
+    gbs = bytes_move * moves_per_s / 1e9
+    tf = flop_move * moves_per_s / 1e12
+    return {"bytes_per_move": bytes_move, "achieved_gbs": gbs, "hbm_peak_gbs": hbm_peak,
+            "hbm_frac": gbs / hbm_peak, "hbm_basis": hbm_basis, "flop_per_move": flop_move,
+            "achieved_tflops": tf, "fp32_frac_of_measured": tf / peaks["fp32_tflops"]}
+
+
 def ranks_max(vals, world):
     """Element-wise maximum of per-rank timings over all ranks (host tensors:
     the process group is gloo, used for the barrier and this maximum only)."""
@@ -258,6 +286,10 @@ def run_ours(args, rank, world, local_rank):
     def max_over_ranks(vals):
         return ranks_max(vals, world)
 
+    # measured arithmetic peaks (a few ms, before any timed region)
+    peaks = ewald.measure_peaks()
+    hbm_peak, hbm_basis = measured_hbm()
+
     # ---- mixed precision, batched: the headline
     ctx, b = make("mixed")
     info = ctx.info()
@@ -297,14 +329,18 @@ def run_ours(args, rank, world, local_rank):
                          % (W * (N * dim * 8 + info["n_runs"] * info["run_len"] * 16) / 1e6),
                    "parallelism": "walker replicas, %d GPU(s)" % world},
         "moves": {"value": moves_per_s, "unit": "move dE/s (propose+accept)",
-                  "ms_per_round": t_m / max(K * M, 1)},
+                  "ms_per_round": t_m / max(K * M, 1),
+                  "roofline": move_roofline(info, w, W, moves_per_s, float(np.mean(acc)), peaks, hbm_peak,
+                                            hbm_basis)},
         "kernel_ms_per_launch": kernel_ms,
         "roofline": {"bound": "alu", "kernel": "k_real<float,%d>" % dim, "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal)",
                      "work": "%d flop per real-space term inside r_c, %.4g terms per launch"
                              % (FLOP_REAL_TERM, terms),
-                     "sfac_tflops": FLOP_G_TERM * N * info["n_g_half"] * W / (sf_ms / sf_n / 1e3) / 1e12},
+                     "sfac_tflops": FLOP_G_TERM * N * info["n_g_half"] * W / (sf_ms / sf_n / 1e3) / 1e12,
+                     "peak_measured": peaks["fp32_tflops"], "frac_of_measured": achieved / peaks["fp32_tflops"],
+                     "peaks_measured": dict(peaks, basis="multiply-add chains, all SMs (ewald_measure_peaks)")},
         "clocks": clk, "gpu_launches": launches,
     }
     b.close()
@@ -345,10 +381,17 @@ def run_ours(args, rank, world, local_rank):
                               "gate": 1e-6, "walkers": int(W),
                               "measure": "|E_mixed - E_fp64| / max(|E|, 1e-2 S) per walker; the FP64 path "
                                          "(cutoffs at 1e-16) is within 1e-12 of the oracle"}
+        i64 = ctx.info()
+        r64_ms, r64_n = f_t["real"]
+        a64 = expected_real_terms(i64, w) * W * FLOP_REAL_TERM / (r64_ms / r64_n / 1e3) / 1e12
         result["fp64"] = {"value": world * W * fs / (f_e / 1e3), "unit": "walker energies/s",
                           "moves": world * W * M * fs / (f_m / 1e3) if M else None,
                           "steps": fs, "kernel_ms_per_launch":
-                              {k: round(v[0] / max(v[1], 1), 3) for k, v in f_t.items() if v[1]}}
+                              {k: round(v[0] / max(v[1], 1), 3) for k, v in f_t.items() if v[1]},
+                          "roofline": {"bound": "alu", "kernel": "k_real<double,%d>" % dim, "achieved": a64,
+                                       "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                                       "frac": a64 / peaks["fp64_tflops"],
+                                       "peak_basis": "measured FP64 FMA rate (ewald_measure_peaks)"}}
         result["mixed_over_fp64"] = energies_per_s / result["fp64"]["value"]
         b.close()
         ctx.close()

@@ -262,6 +262,15 @@ int ewald_energy_noalloc(ewald_ctx *ctx, const double *pos, int n_walkers, doubl
 int ewald_set_timing(ewald_ctx *ctx, int enable);
 int ewald_get_timing(ewald_ctx *ctx, double *ms, long long *launches);
 
+/* Measured arithmetic peaks of the current GPU, for the rooflines of the
+ * ALU-bound kernels: FP32 FMA and FP64 FMA in TFLOP/s (2 flop per FMA) and
+ * the special-function unit's rsqrt rate in Tops/s.  Runs a few
+ * milliseconds of multiply-add chains on a private stream and synchronises
+ * it; any output pointer may be NULL.  Not part of the method: a
+ * measurement aid (the paper quantifies GPU performance against peaks in
+ * Sec. 4). */
+int ewald_measure_peaks(double *fp32_tflops, double *fp64_tflops, double *mufu_tops);
+
 #ifdef __cplusplus
 }
 #endif

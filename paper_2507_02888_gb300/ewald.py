@@ -95,6 +95,7 @@ SIGNATURES = [
     ("ewald_autotune", _c_int, [_vp, ctypes.c_char_p, _vp]),
     ("ewald_set_timing", _c_int, [_vp, _c_int]),
     ("ewald_get_timing", _c_int, [_vp, _vp, _vp]),
+    ("ewald_measure_peaks", _c_int, [_vp, _vp, _vp]),
 ]
 
 KERNELS = ["ingest", "sfac", "real", "combine", "propose", "accept", "resum"]
@@ -344,6 +345,14 @@ class Multi:
             self.close()
         except Exception:
             pass
+
+
+def measure_peaks():
+    """Measured FP32 FMA and FP64 FMA TFLOP/s and rsqrt Tops/s of the current GPU."""
+    load()
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ewald_measure_peaks(ctypes.addressof(a), ctypes.addressof(b), ctypes.addressof(c)))
+    return {"fp32_tflops": a.value, "fp64_tflops": b.value, "rsqrt_tops": c.value}
 
 
 def context_for(workload, precision="fp64", stream=None, **kw):
