@@ -212,6 +212,10 @@ int ewald_server_step(ewald_server *srv, int *n_active, int *n_queued);
  * completion as seen by the host. */
 int ewald_server_result(ewald_server *srv, int request_id, double *energies, int *n_accepted,
                         double *latency_ms);
+/* Ids of requests that finished since the last call (up to max_ids, the
+ * rest on the next call; *n receives the count): a host loop can fetch just
+ * those results instead of polling every pending request. */
+int ewald_server_completed(ewald_server *srv, int *ids, int max_ids, int *n);
 /* Wait until everything queued on the server's stream has run. */
 int ewald_server_drain(ewald_server *srv);
 const char *ewald_server_error_message(const ewald_server *srv);

@@ -66,22 +66,24 @@ struct SlotSum<float> {
 template <typename R, int DIM, int L>
 __device__ __forceinline__ void sfac_runs(const SfacTile<R> &t, int4 rn, int dir, SlotSum<R> *ax, SlotSum<R> *ay) {
     using C = Cx<R>;
+    // the run's first term q e^{iG.r} (the charge rides along the recurrence)
     auto start = [&](int e, C &z, C &step) {
         z = cmul(t.P1[(size_t)e * t.W1 + rn.x + t.n1max], t.P2[(size_t)e * t.W2 + rn.y + t.n2max]);
         if (DIM == 3) z = cmul(z, t.P3[(size_t)e * t.W3 + rn.z]);
+        const R q = t.tp[e].q;
+        z = {q * z.x, q * z.y};
         step = t.P1[(size_t)e * t.W1 + t.n1max + dir];
     };
     int e = 0;
     for (; e + 1 < t.ne; e += 2) {
-        const R qa = t.tp[e].q, qb = t.tp[e + 1].q;
         C za, sa, zb, sb;
         start(e, za, sa);
         start(e + 1, zb, sb);
 #pragma unroll
         for (int r = 0; r < L; ++r) {
             if (r < rn.w) {
-                ax[r].add(qa * za.x + qb * zb.x);
-                ay[r].add(qa * za.y + qb * zb.y);
+                ax[r].add(za.x + zb.x);
+                ay[r].add(za.y + zb.y);
                 if (r + 1 < L) {
                     za = cmul(za, sa);
                     zb = cmul(zb, sb);
@@ -90,14 +92,13 @@ __device__ __forceinline__ void sfac_runs(const SfacTile<R> &t, int4 rn, int dir
         }
     }
     if (e < t.ne) {
-        const R q = t.tp[e].q;
         C z, st;
         start(e, z, st);
 #pragma unroll
         for (int r = 0; r < L; ++r) {
             if (r < rn.w) {
-                ax[r].add(q * z.x);
-                ay[r].add(q * z.y);
+                ax[r].add(z.x);
+                ay[r].add(z.y);
                 if (r + 1 < L) z = cmul(z, st);
             }
         }

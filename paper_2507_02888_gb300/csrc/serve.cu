@@ -65,6 +65,8 @@ struct ewald_server {
     std::vector<SysDev> sys_host;
     std::map<int, Req> reqs;
     std::deque<int> queue;
+    std::vector<int> draining;   // retired requests whose results are on their way to the host
+    std::vector<int> completed;  // finished since the last ewald_server_completed
     std::vector<int> slot_req;  // slot -> request id or -1
     std::vector<std::pair<int, int>> acc_free;  // free ranges [base, base + len) of the n_acc array
     int next_id = 1;
@@ -348,11 +350,18 @@ int ewald_server_step(ewald_server *s, int *n_active, int *n_queued) {
     if (!s) return EWALD_ERR_ARG;
     cudaError_t e;
     // 1. requests whose results have arrived
-    for (auto &kv : s->reqs) {
-        Req &r = kv.second;
+    for (size_t i = 0; i < s->draining.size();) {
+        Req &r = s->reqs[s->draining[i]];
         if (r.state == 2 && cudaEventQuery(r.ev_done) == cudaSuccess) {
             r.state = 3;
             r.t_done = now_s();
+        }
+        if (r.state == 3) {
+            s->completed.push_back(r.id);
+            s->draining[i] = s->draining.back();
+            s->draining.pop_back();
+        } else {
+            ++i;
         }
     }
     // 2. retire finished requests (copies and frees are stream-ordered)
@@ -373,6 +382,7 @@ int ewald_server_step(ewald_server *s, int *n_active, int *n_queued) {
         for (void *p : r.dev) cudaFreeAsync(p, s->stream);
         r.dev.clear();
         r.state = 2;
+        s->draining.push_back(r.id);
         s->slot_req[slot] = -1;
         s->used_walkers -= r.W;
         s->used_bytes -= r.bytes;
@@ -480,6 +490,15 @@ int ewald_server_result(ewald_server *s, int request_id, double *energies, int *
     if (energies) std::memcpy(energies, r.pin_e, sizeof(double) * r.W);
     if (n_accepted) std::memcpy(n_accepted, r.pin_acc, sizeof(int) * r.W);
     if (latency_ms) *latency_ms = 1e3 * (r.t_done - r.t_submit);
+    return EWALD_OK;
+}
+
+int ewald_server_completed(ewald_server *s, int *ids, int max_ids, int *n) {
+    if (!s || !n || (max_ids > 0 && !ids)) return EWALD_ERR_ARG;
+    const int k = std::min<int>(max_ids, (int)s->completed.size());
+    for (int i = 0; i < k; ++i) ids[i] = s->completed[i];
+    s->completed.erase(s->completed.begin(), s->completed.begin() + k);
+    *n = k;
     return EWALD_OK;
 }
 

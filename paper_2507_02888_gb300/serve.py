@@ -22,6 +22,7 @@ SIGNATURES = [
                                      ctypes.c_ulonglong, ctypes.POINTER(_c_int)]),
     ("ewald_server_step", _c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     ("ewald_server_result", _c_int, [_vp, _c_int, _vp, _vp, ctypes.POINTER(_c_double)]),
+    ("ewald_server_completed", _c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int)]),
     ("ewald_server_drain", _c_int, [_vp]),
     ("ewald_server_error_message", ctypes.c_char_p, [_vp]),
 ]
@@ -72,6 +73,13 @@ class Server:
         self._check(_lib().ewald_server_step(self._h, ctypes.byref(a), ctypes.byref(q)))
         return a.value, q.value
 
+    def completed(self, max_ids=4096):
+        """Ids of the requests that finished since the last call."""
+        ids = np.zeros(max_ids, dtype=np.int32)
+        n = _c_int()
+        self._check(_lib().ewald_server_completed(self._h, _vp(ids.ctypes.data), max_ids, ctypes.byref(n)))
+        return ids[:n.value].tolist()
+
     def result(self, rid):
         """(energies [W], accepted [W], latency ms) once done, else None."""
         W = self._W[rid]
@@ -107,7 +115,7 @@ def run_stream(server, requests, time_limit=600.0):
     per-request results, latencies (ms), total walker-moves and elapsed time.
     """
     order = sorted(range(len(requests)), key=lambda i: requests[i][0])
-    ids, done, lat = {}, {}, {}
+    ids, done, lat, by_id = {}, {}, {}, {}
     pending = set()
     t0 = time.perf_counter()
     nxt = 0
@@ -119,15 +127,18 @@ def run_stream(server, requests, time_limit=600.0):
         while nxt < len(order) and requests[order[nxt]][0] <= now:
             t, ctx, pos, steps, sigma, seed = requests[order[nxt]]
             ids[order[nxt]] = server.submit(ctx, pos, steps, sigma, 0.5, seed)
+            by_id[ids[order[nxt]]] = order[nxt]
             pending.add(order[nxt])
             nxt += 1
         active, queued = server.step()
-        for i in list(pending):
-            r = server.result(ids[i])
-            if r is not None:
-                done[i] = r
-                lat[i] = r[2]
-                pending.discard(i)
+        for rid in server.completed():
+            i = by_id.get(rid)
+            if i is None:
+                continue
+            r = server.result(rid)
+            done[i] = r
+            lat[i] = r[2]
+            pending.discard(i)
         if not active and not queued and nxt < len(order):
             time.sleep(max(0.0, min(0.001, requests[order[nxt]][0] - (time.perf_counter() - t0))))
     server.drain()

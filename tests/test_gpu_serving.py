@@ -162,3 +162,13 @@ def test_admission_respects_walker_budget(mods):
             break
     assert len(out) == 3
     assert max(seen_active) == 1                            # 6 + 6 > 8 walkers: one at a time
+    # every finished request is reported by completed() exactly once
+    got = []
+    for _ in range(100):
+        srv.step()
+        got += srv.completed()
+        if len(got) >= 3:
+            break
+    assert sorted(got) == sorted(ids)
+    srv.step()
+    assert srv.completed() == []
