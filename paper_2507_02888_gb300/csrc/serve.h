@@ -6,7 +6,7 @@
 
 namespace ewald {
 
-constexpr int kServeMinBlocks = 3;  // resident serving CTAs per SM the registers are sized for
+constexpr int kServeMinBlocks = 4;  // resident serving CTAs per SM the registers are sized for
 
 // One active request: its walkers' state and its move stream.
 struct SlotDev {
