@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-configs", action="store_true", help="skip the per-config table (c0, c2, c3)")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-requests-fp64", type=int, default=120)
     return p.parse_args()
@@ -441,6 +442,8 @@ def run_ours(args, rank, world, local_rank):
         ctx.close()
 
     # ---- batched form (uneven systems in one persistent launch) and serving form
+    if not args.no_configs:
+        result["configs"] = run_configs(stream)
     if not args.no_batched:
         result["batched"] = run_batched(stream, 5)
     if not args.no_serving:
@@ -496,6 +499,65 @@ def run_batched(stream, steps):
             "workload": "diamond_3x3x3 (W=1024) + heg2d_hex_n338 (W=2048), one persistent launch",
             "separate_batches": Wt * steps / (t_sep / 1e3), "steps": steps,
             "tiling": [{"pair_tile": t["pair_tile"], "subcell_bits": t["subcell_bits"]} for t in tune]}
+
+
+def run_configs(stream, steps=3, moves=4):
+    """The other single-system workloads at their own sizes, each in both
+    precisions: walker energies/s, move dE/s (propose + accept rounds) and the
+    mixed path's per-walker error against the FP64 path (floor as in the
+    tests).  Device-resident inputs; every step re-evaluates the same
+    configurations (each round's moves put the same particles at the same
+    places)."""
+    import torch
+    from paper_2507_02888_gb300 import ewald, inputs
+    out = {}
+    for name in ["heg3d_sc_n54", "heg2d_hex_n338", "diamond_3x3x3"]:
+        w = inputs.workload(name)
+        W, N, dim = w["n_walkers"], w["n"], w["dim"]
+        rng = np.random.default_rng(77)
+        ks, disp, acc = inputs.move_stream(rng, W, N, moves, dim, w["sigma"])
+        k_d = torch.tensor(ks, device="cuda")
+        rn_d = torch.tensor(w["pos"][np.arange(W)[None, :], ks] + disp, device="cuda")
+        acc_d = torch.tensor(acc, device="cuda")
+        pos_d = torch.tensor(w["pos"], device="cuda")
+        e_d = torch.empty(W, dtype=torch.float64, device="cuda")
+        de_d = torch.empty(W, dtype=torch.float64, device="cuda")
+        row, energies = {"walkers": W, "n": N, "n_fixed": len(w["fixed_q"]), "dim": dim}, {}
+        for prec in ("mixed", "fp64"):
+            ctx = ewald.context_for(w, precision=prec, stream=stream)
+            b = ewald.Batch(ctx, W)
+            b.set_positions(pos_d)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            with torch.cuda.stream(stream):
+                for _ in range(2):                      # warm-up, and the moved configuration
+                    b.energy(e_d)
+                    for m in range(moves):
+                        b.propose(k_d[m], rn_d[m], de_d)
+                        b.accept(acc_d[m])
+                ev[0].record(stream)
+                for _ in range(steps):
+                    b.energy(e_d)
+                ev[1].record(stream)
+                for _ in range(steps):
+                    for m in range(moves):
+                        b.propose(k_d[m], rn_d[m], de_d)
+                        b.accept(acc_d[m])
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+            comp = b.components()
+            energies[prec] = (e_d.cpu().numpy().copy(), comp)
+            row[prec] = {"walker_energies_per_s": W * steps / (ev[0].elapsed_time(ev[1]) / 1e3),
+                         "move_de_per_s": W * moves * steps / (ev[1].elapsed_time(ev[2]) / 1e3),
+                         "r_cutoff": ctx.info()["r_cutoff"]}
+            b.close()
+            ctx.close()
+        em, (ef, cf) = energies["mixed"][0], energies["fp64"]
+        floor = np.maximum(np.abs(cf.sum(axis=1)),
+                           1e-2 * (np.abs(cf[:, 0]) + np.abs(cf[:, 2]) + np.abs(cf[:, 1] + cf[:, 3]) + np.abs(cf[:, 4])))
+        rel = (em - ef) / floor
+        row["mixed_vs_fp64"] = {"max": float(np.max(np.abs(rel))), "mean": float(np.mean(rel))}
+        out[name] = row
+    return out
 
 
 SERVE_SYSTEMS = ["heg3d_sc_n54", "heg3d_sc_n128", "heg2d_hex_n338", "heg3d_sc_n512", "heg3d_fcc_n1024",
