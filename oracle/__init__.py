@@ -4,8 +4,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The GPU library never imports it and
 the oracle imports nothing from the GPU library.
 
-Functions follow the paper's Sec. 2.2, Eqs. (2)-(6); see ``ewald_oracle.c``
-for the formulas.  Every call takes positions as a ``(n, dim)`` float64 array
+Functions follow the paper's Sec. 2.2, Eqs. (2)-(6), and for the two-body
+plane-wave Jastrow term Sec. 2.3, Eqs. (7) and (9); see ``ewald_oracle.c`` for
+the formulas.  Every call takes positions as a ``(n, dim)`` float64 array
 of Cartesian coordinates and charges as an ``(n,)`` float64 array.
 """
 import ctypes
@@ -55,6 +56,10 @@ def _load():
             lib.oracle_gcount.argtypes = [c_int, dp, c_double]
             lib.oracle_gcount.restype = ctypes.c_long
             lib.oracle_cutoffs.argtypes = [c_int, c_double, c_double, dp, dp]
+            lib.oracle_jastrow_stars.argtypes = [c_int, dp, c_int, c_int, ip, ip, ip]
+            lib.oracle_jastrow_p.argtypes = [c_int, dp, c_int, dp, c_int, dp, dp, dp, dp]
+            lib.oracle_jastrow_stars.restype = ctypes.c_int
+            lib.oracle_jastrow_p.restype = ctypes.c_int
             for f in (lib.oracle_energy, lib.oracle_delta_e, lib.oracle_rho_at,
                       lib.oracle_recip_pairsum, lib.oracle_cutoffs):
                 f.restype = ctypes.c_int
@@ -144,3 +149,33 @@ def gcount(dim, lattice, g_c):
     """Number of G != 0 with |G| <= g_c, counting +G and -G."""
     lat = _f64(lattice, (dim, dim))
     return int(_load().oracle_gcount(dim, _dp(lat), g_c))
+
+
+def jastrow_stars(dim, lattice, n_stars):
+    """Every G of the first n_stars shells of equal |G| (both signs):
+    (nvec (n_g, dim) integer reciprocal coordinates, star (n_g,) shell index)."""
+    lat = _f64(lattice, (dim, dim))
+    n_g = ctypes.c_int()
+    ip = ctypes.POINTER(ctypes.c_int)
+    _check(_load().oracle_jastrow_stars(dim, _dp(lat), int(n_stars), 0, ctypes.byref(n_g), None, None))
+    nv = np.zeros((n_g.value, dim), dtype=np.int32)
+    st = np.zeros(n_g.value, dtype=np.int32)
+    _check(_load().oracle_jastrow_stars(dim, _dp(lat), int(n_stars), n_g.value, ctypes.byref(n_g),
+                                        nv.ctypes.data_as(ip), st.ctypes.data_as(ip)))
+    return nv, st
+
+
+def jastrow_p(dim, lattice, pos, a):
+    """J_p = sum_{i<j} p(r_i - r_j) with p(r) = sum_m a_m sum_{G in star m, one of +-G} cos(G.r),
+    and its gradient (n, dim) and Laplacian (n,) with respect to each particle."""
+    lat = _f64(lattice, (dim, dim))
+    pos = _f64(pos)
+    n = pos.shape[0]
+    pos = pos.reshape(n, dim)
+    a = _f64(a).reshape(-1)
+    j = ctypes.c_double()
+    grad = np.zeros((n, dim))
+    lap = np.zeros(n)
+    _check(_load().oracle_jastrow_p(dim, _dp(lat), n, _dp(pos), a.size, _dp(a), ctypes.byref(j), _dp(grad),
+                                    _dp(lap)))
+    return j.value, grad, lap

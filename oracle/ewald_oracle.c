@@ -440,3 +440,153 @@ int oracle_cutoffs(int dim, double alpha, double tol, double *r_c, double *g_c) 
     *g_c = dim == 3 ? 2.0 * alpha * sqrt(-log(tol)) : 2.0 * alpha * x;
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------
+ * Two-body plane-wave Jastrow term p (paper Sec. 2.3, Eqs. (7), (9)):
+ *
+ *   J_p = sum_{i<j} p(r_i - r_j),   p(r) = sum_{m=1}^{N_p} a_m sum_{G in star_m^+} cos(G.r)
+ *
+ * A star is read here as a shell of simulation-cell reciprocal-lattice
+ * vectors of equal length (relative tolerance 1e-9), shells counted from the
+ * shortest nonzero |G|; star_m^+ holds one of each +-G pair, so the oracle
+ * sums the whole shell (both signs) with a factor 1/2.  cos is periodic, so
+ * r_i - r_j needs no wrapping.  Derivatives by particle i:
+ *
+ *   grad_i J_p = sum_{j != i} sum_m a_m sum_{G in star_m^+} (-sin(G.(r_i - r_j))) G
+ *   lap_i  J_p = sum_{j != i} sum_m a_m sum_{G in star_m^+} (-|G|^2) cos(G.(r_i - r_j))
+ *
+ * Plain double loops over pairs and G vectors, cos and sin of each phase.
+ * ---------------------------------------------------------------------- */
+
+typedef struct {
+    double *g;
+    long n, cap;
+} glist_t;
+
+static void visit_collect(const double *G, double g, const int *nvec, void *vctx) {
+    (void)G;
+    (void)nvec;
+    glist_t *l = (glist_t *)vctx;
+    if (l->n == l->cap) {
+        l->cap = l->cap ? 2 * l->cap : 256;
+        l->g = (double *)realloc(l->g, (size_t)l->cap * sizeof(double));
+    }
+    l->g[l->n++] = g;
+}
+
+static int cmp_double(const void *a, const void *b) {
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Shell radii: radius[m] for m = 0 .. n_stars-1.  Grows the search sphere
+ * until it holds n_stars shells completely (all G with |G| <= g are visited). */
+static int star_radii(const cell_t *c, int n_stars, double *radius) {
+    double g = 0.0;
+    for (int k = 0; k < c->dim; ++k) g = fmax(g, norm(c->dim, c->b[k]));
+    for (int iter = 0; iter < 40; ++iter, g *= 1.5) {
+        glist_t l = {NULL, 0, 0};
+        for_each_g(c, g, visit_collect, &l);
+        qsort(l.g, (size_t)l.n, sizeof(double), cmp_double);
+        int m = 0;
+        for (long i = 0; i < l.n && m < n_stars; ++i)
+            if (m == 0 || l.g[i] > radius[m - 1] * (1.0 + 1e-9)) radius[m++] = l.g[i];
+        free(l.g);
+        if (m >= n_stars) return ORC_OK;
+    }
+    return ORC_ERR_ARG;
+}
+
+static int star_of(const double *radius, int n_stars, double g) {
+    for (int m = 0; m < n_stars; ++m)
+        if (fabs(g / radius[m] - 1.0) <= 1e-9) return m;
+    return -1;
+}
+
+/* Every G of the first n_stars shells (both signs): nvec[i][dim] integer
+ * coordinates on the reciprocal basis and star[i] (0-based shell index).
+ * *n_g receives the count; at most max_g entries are written. */
+typedef struct {
+    int dim, n_stars, max_g, count;
+    const double *radius;
+    int *nvec, *star;
+} starlist_t;
+
+static void visit_star_list(const double *G, double g, const int *nvec, void *vctx) {
+    (void)G;
+    starlist_t *s = (starlist_t *)vctx;
+    int m = star_of(s->radius, s->n_stars, g);
+    if (m < 0) return;
+    if (s->count < s->max_g) {
+        for (int k = 0; k < s->dim; ++k) s->nvec[s->count * s->dim + k] = nvec[k];
+        s->star[s->count] = m;
+    }
+    s->count++;
+}
+
+int oracle_jastrow_stars(int dim, const double *lattice, int n_stars, int max_g, int *n_g, int *nvec,
+                         int *star) {
+    cell_t c;
+    if (n_stars < 1 || !n_g) return ORC_ERR_ARG;
+    int st = make_cell(dim, lattice, &c);
+    if (st) return st;
+    double *radius = (double *)malloc((size_t)n_stars * sizeof(double));
+    st = star_radii(&c, n_stars, radius);
+    if (!st) {
+        starlist_t s = {dim, n_stars, max_g, 0, radius, nvec, star};
+        for_each_g(&c, radius[n_stars - 1] * (1.0 + 1e-9), visit_star_list, &s);
+        *n_g = s.count;
+    }
+    free(radius);
+    return st;
+}
+
+typedef struct {
+    int dim, n, n_stars;
+    const double *pos, *a, *radius;
+    ksum_t j;
+    ksum_t *grad, *lap;
+} jp_ctx;
+
+static void visit_jastrow(const double *G, double g, const int *nvec, void *vctx) {
+    (void)nvec;
+    jp_ctx *c = (jp_ctx *)vctx;
+    int m = star_of(c->radius, c->n_stars, g);
+    if (m < 0) return;
+    const double w = 0.5 * c->a[m];  /* the whole shell, both signs */
+    const int dim = c->dim;
+    for (int i = 0; i < c->n; ++i)
+        for (int j = 0; j < c->n; ++j) {
+            if (i == j) continue;
+            double ph = 0.0;
+            for (int k = 0; k < dim; ++k) ph += G[k] * (c->pos[i * dim + k] - c->pos[j * dim + k]);
+            const double cs = cos(ph), sn = sin(ph);
+            if (i < j) kadd(&c->j, w * cs);
+            if (c->grad)
+                for (int k = 0; k < dim; ++k) kadd(&c->grad[i * dim + k], -w * sn * G[k]);
+            if (c->lap) kadd(&c->lap[i], -w * g * g * cs);
+        }
+}
+
+int oracle_jastrow_p(int dim, const double *lattice, int n, const double *pos, int n_stars, const double *a,
+                     double *j_out, double *grad, double *lap) {
+    cell_t c;
+    if (n < 1 || n_stars < 1 || !pos || !a || !j_out) return ORC_ERR_ARG;
+    int st = make_cell(dim, lattice, &c);
+    if (st) return st;
+    double *radius = (double *)malloc((size_t)n_stars * sizeof(double));
+    ksum_t *gs = grad ? (ksum_t *)calloc((size_t)n * dim, sizeof(ksum_t)) : NULL;
+    ksum_t *ls = lap ? (ksum_t *)calloc((size_t)n, sizeof(ksum_t)) : NULL;
+    st = star_radii(&c, n_stars, radius);
+    if (!st) {
+        jp_ctx ctx = {dim, n, n_stars, pos, a, radius, {0, 0}, gs, ls};
+        for_each_g(&c, radius[n_stars - 1] * (1.0 + 1e-9), visit_jastrow, &ctx);
+        *j_out = kval(&ctx.j);
+        for (int i = 0; grad && i < n * dim; ++i) grad[i] = kval(&gs[i]);
+        for (int i = 0; lap && i < n; ++i) lap[i] = kval(&ls[i]);
+    }
+    free(radius);
+    free(gs);
+    free(ls);
+    return st;
+}
