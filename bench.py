@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-configs", action="store_true", help="skip the per-config table (c0, c2, c3)")
+    p.add_argument("--no-jastrow", action="store_true", help="skip the two-body plane-wave Jastrow term")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-requests-fp64", type=int, default=120)
     return p.parse_args()
@@ -444,6 +445,8 @@ def run_ours(args, rank, world, local_rank):
     # ---- batched form (uneven systems in one persistent launch) and serving form
     if not args.no_configs:
         result["configs"] = run_configs(stream)
+    if not args.no_jastrow:
+        result["jastrow_p"] = run_jastrow(stream, args.workload)
     if not args.no_batched:
         result["batched"] = run_batched(stream, 5)
     if not args.no_serving:
@@ -557,6 +560,42 @@ def run_configs(stream, steps=3, moves=4):
         rel = (em - ef) / floor
         row["mixed_vs_fp64"] = {"max": float(np.max(np.abs(rel))), "mean": float(np.mean(rel))}
         out[name] = row
+    return out
+
+
+def run_jastrow(stream, workload, n_stars=8, steps=3):
+    """Two-body plane-wave Jastrow term p (Sec. 2.3, Eq. (9)) of every walker
+    with gradients and Laplacians, both precisions: walker evaluations/s and
+    phase evaluations/s (each (electron, G) phase is evaluated twice: once for
+    rho(G), once for the electron's derivatives)."""
+    import torch
+    from paper_2507_02888_gb300 import ewald, inputs
+    w = inputs.workload(workload)
+    W, N, dim = w["n_walkers"], w["n"], w["dim"]
+    a = 0.2 * (-0.4) ** np.arange(n_stars)
+    pos_d = torch.tensor(w["pos"], device="cuda")
+    j = torch.empty(W, dtype=torch.float64, device="cuda")
+    g = torch.empty((W, N, dim), dtype=torch.float64, device="cuda")
+    lap = torch.empty((W, N), dtype=torch.float64, device="cuda")
+    out = {"workload": workload, "walkers": W, "n_stars": n_stars}
+    for prec in ("mixed", "fp64"):
+        ctx = ewald.context_for(w, precision=prec, stream=stream)
+        n_g = ctx.set_jastrow_p(a)
+        b = ewald.Batch(ctx, W)
+        b.set_positions(pos_d)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(stream):
+            b.jastrow_p(j, g, lap)
+            ev[0].record(stream)
+            for _ in range(steps):
+                b.jastrow_p(j, g, lap)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+        t = ev[0].elapsed_time(ev[1]) / 1e3
+        out[prec] = {"walker_evaluations_per_s": W * steps / t, "n_g_half": n_g,
+                     "phase_evaluations_per_s": 2.0 * W * N * n_g * steps / t}
+        b.close()
+        ctx.close()
     return out
 
 

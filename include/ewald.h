@@ -266,6 +266,23 @@ int ewald_energy_noalloc(ewald_ctx *ctx, const double *pos, int n_walkers, doubl
 int ewald_set_timing(ewald_ctx *ctx, int enable);
 int ewald_get_timing(ewald_ctx *ctx, double *ms, long long *launches);
 
+/* Two-body plane-wave Jastrow term (paper Sec. 2.3, Eqs. (7), (9), (10)):
+ *   J_p = sum_{i<j} p(r_i - r_j),  p(r) = sum_{m=1}^{n_stars} a_m sum_{G in star_m^+} cos(G.r)
+ * over the mobile particles (electrons) of each walker, with a star read as
+ * a shell of simulation-cell reciprocal-lattice vectors of equal |G| counted
+ * from the shortest, star_m^+ one of each +-G pair.
+ * ewald_jastrow_p_set stores the stars' G vectors and coefficients a[n_stars]
+ * (host memory, 1 <= n_stars <= 64) on the context; ewald_jastrow_p_count
+ * gives the number of G vectors kept.  ewald_jastrow_p writes, per walker,
+ * j_out[W] and optionally grad_out[W][N][dim] = dJ_p/dr_i and
+ * lap_out[W][N] = Laplacian of J_p with respect to r_i (either may be NULL);
+ * all three on the device or on the host together (on_device).  Positions
+ * are the batch's; phases are exact (fixed-point) in both precisions, sums
+ * in FP64.  Errors: EWALD_ERR_STATE without positions or stars. */
+int ewald_jastrow_p_set(ewald_ctx *ctx, int n_stars, const double *a);
+int ewald_jastrow_p_count(const ewald_ctx *ctx, int *n_g);
+int ewald_jastrow_p(ewald_batch *b, double *j_out, double *grad_out, double *lap_out, int on_device);
+
 /* Measured arithmetic peaks of the current GPU, for the rooflines of the
  * ALU-bound kernels: FP32 FMA and FP64 FMA in TFLOP/s (2 flop per FMA) and
  * the special-function unit's rsqrt rate in Tops/s.  Runs a few

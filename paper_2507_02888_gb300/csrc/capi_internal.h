@@ -23,6 +23,11 @@ struct ewald_ctx {
     bool destroy_pending = false;
     int last_error = EWALD_OK;
     std::string why;
+    // two-body plane-wave Jastrow term (jastrow.cu): the stars' G vectors,
+    // one of each +-G pair
+    int jp_n_g = 0, jp_n_stars = 0;
+    int4 *d_jp_nvec = nullptr;     // (n1, n2, n3, star)
+    double4 *d_jp_gvec = nullptr;  // (Gx, Gy, Gz, a of its star)
     // kernel timers
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;

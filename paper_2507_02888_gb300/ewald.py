@@ -96,6 +96,9 @@ SIGNATURES = [
     ("ewald_set_timing", _c_int, [_vp, _c_int]),
     ("ewald_get_timing", _c_int, [_vp, _vp, _vp]),
     ("ewald_measure_peaks", _c_int, [_vp, _vp, _vp]),
+    ("ewald_jastrow_p_set", _c_int, [_vp, _c_int, _vp]),
+    ("ewald_jastrow_p_count", _c_int, [_vp, ctypes.POINTER(_c_int)]),
+    ("ewald_jastrow_p", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
 ]
 
 KERNELS = ["ingest", "sfac", "real", "combine", "propose", "accept", "resum"]
@@ -193,6 +196,15 @@ class Context:
         out = np.zeros((n, self.dim), dtype=np.int32)
         _check(_lib.ewald_get_gvectors(self._h, ctypes.c_void_p(out.ctypes.data)))
         return out
+
+    def set_jastrow_p(self, a):
+        """Stars of the two-body plane-wave Jastrow term with coefficients a[n_stars];
+        returns the number of G vectors kept (one of each +-G pair)."""
+        a = _f64(a)
+        _check(_lib.ewald_jastrow_p_set(self._h, a.size, ctypes.c_void_p(a.ctypes.data)), self)
+        n = _c_int()
+        _check(_lib.ewald_jastrow_p_count(self._h, ctypes.byref(n)), self)
+        return n.value
 
     def set_timing(self, enable=True):
         _check(_lib.ewald_set_timing(self._h, int(bool(enable))))
@@ -292,6 +304,20 @@ class Batch:
         p, dev = _ptr(out)
         _check(_lib.ewald_batch_get_rho(self._h, p, dev), self.ctx)
         return out
+
+    def jastrow_p(self, j=None, grad=None, lap=None, derivatives=True):
+        """J_p per walker and (derivatives=True) its gradient [W][N][dim] and
+        Laplacian [W][N] per electron; host arrays unless device tensors are given."""
+        N, dim = self.ctx.n_mobile, self.ctx.dim
+        if j is None:
+            j = np.zeros(self.W)
+            if derivatives:
+                grad, lap = np.zeros((self.W, N, dim)), np.zeros((self.W, N))
+        pj, dev = _ptr(j)
+        pg = _ptr(grad)[0] if grad is not None else None
+        pl = _ptr(lap)[0] if lap is not None else None
+        _check(_lib.ewald_jastrow_p(self._h, pj, pg, pl, dev), self.ctx)
+        return j, grad, lap
 
     def sync(self):
         _check(_lib.ewald_batch_sync(self._h), self.ctx)
