@@ -32,12 +32,18 @@ struct JastrowDev {
     const double4 *gvec;
 };
 
+// shared memory: rho (n_g double2), the electron tile, then (32-byte
+// aligned) the per-G coefficients and rho in R for the derivative pass
+__host__ __device__ inline size_t jp_coef_offset(int n_g, int dim, size_t u_bytes) {
+    return (align16((size_t)n_g * sizeof(double2)) + (size_t)kJpTile * dim * u_bytes + 31) / 32 * 32;
+}
+
 template <typename R, int DIM>
 __global__ void __launch_bounds__(kJpThreads)
     k_jastrow_p(SysDev s, BatchDev b, JastrowDev jd, double *__restrict__ j_out, double *__restrict__ grad,
                 double *__restrict__ lap) {
     using U = typename FP<R>::U;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(32) unsigned char smem[];
     __shared__ double red[kJpThreads / 32];
     double2 *rho = (double2 *)smem;
     U *ut = (U *)(smem + align16((size_t)jd.n_g * sizeof(double2)));
@@ -58,15 +64,16 @@ __global__ void __launch_bounds__(kJpThreads)
         __syncthreads();
         for (int g = tid; g < jd.n_g; g += blockDim.x) {
             const int4 n = jd.nvec[g];
-            double sx = 0.0, sy = 0.0;
+            // tile sums (compensated in FP32), then FP64 across tiles
+            Acc<R> sx, sy;
             for (int e = 0; e < ne; ++e) {
                 R sn, cs;
                 FP<R>::sincospi2(FP<R>::frac(phase(n, ut + e * DIM)), &sn, &cs);
-                sx += (double)cs;
-                sy += (double)sn;
+                sx.add(cs);
+                sy.add(sn);
             }
-            rho[g].x += sx;
-            rho[g].y += sy;
+            rho[g].x += sx.get();
+            rho[g].y += sy.get();
         }
     }
     __syncthreads();
@@ -78,34 +85,52 @@ __global__ void __launch_bounds__(kJpThreads)
     jp = block_sum(jp, red);
     if (tid == 0) j_out[w] = jp;
     if (!grad && !lap) return;
+    // per G: rho and the derivative weights -a G and -a |G|^2, in R
+    using R2 = typename FP<R>::R4;
+    R2 *cf = (R2 *)(smem + jp_coef_offset(jd.n_g, DIM, sizeof(U)));
+    R2 *rr = cf + jd.n_g;
+    for (int g = tid; g < jd.n_g; g += blockDim.x) {
+        const double4 G = jd.gvec[g];
+        R2 c, r;
+        c.x = (R)(-G.w * G.x);
+        c.y = (R)(-G.w * G.y);
+        c.z = (R)(-G.w * G.z);
+        c.w = (R)(-G.w * (G.x * G.x + G.y * G.y + G.z * G.z));
+        r.x = (R)rho[g].x;
+        r.y = (R)rho[g].y;
+        r.z = r.w = 0;
+        cf[g] = c;
+        rr[g] = r;
+    }
+    __syncthreads();
     for (int e = tid; e < N; e += blockDim.x) {
         U u[3] = {0, 0, 0};
         for (int k = 0; k < DIM; ++k) u[k] = FP<R>::from64(b.u[((size_t)w * DIM + k) * s.mob_stride + e]);
-        double gs[3] = {0.0, 0.0, 0.0}, ls = 0.0;
+        Acc<R> gs[3], ls;
         for (int g = 0; g < jd.n_g; ++g) {
             const int4 n = jd.nvec[g];
             R sn, cs;
             FP<R>::sincospi2(FP<R>::frac(phase(n, u)), &sn, &cs);
-            const double2 r = rho[g];
+            const R2 r = rr[g], c = cf[g];
             // e^{iG.r_e} conj(rho) = (cs r.x + sn r.y) + i (sn r.x - cs r.y)
-            const double re = (double)cs * r.x + (double)sn * r.y;
-            const double im = (double)sn * r.x - (double)cs * r.y;
-            const double4 G = jd.gvec[g];
-            gs[0] -= G.w * G.x * im;
-            gs[1] -= G.w * G.y * im;
-            if (DIM == 3) gs[2] -= G.w * G.z * im;
-            ls -= G.w * (G.x * G.x + G.y * G.y + G.z * G.z) * (re - 1.0);
+            const R re = cs * r.x + sn * r.y;
+            const R im = sn * r.x - cs * r.y;
+            gs[0].add(c.x * im);
+            gs[1].add(c.y * im);
+            if (DIM == 3) gs[2].add(c.z * im);
+            ls.add(c.w * (re - R(1)));
         }
         const size_t o = (size_t)w * N + e;
         if (grad)
-            for (int k = 0; k < DIM; ++k) grad[o * DIM + k] = gs[k];
-        if (lap) lap[o] = ls;
+            for (int k = 0; k < DIM; ++k) grad[o * DIM + k] = gs[k].get();
+        if (lap) lap[o] = ls.get();
     }
 }
 
 static size_t jastrow_smem(const SysDev &s, int n_g, int precision) {
     const size_t u = precision == EWALD_FP64 ? sizeof(unsigned long long) : sizeof(unsigned int);
-    return align16((size_t)n_g * sizeof(double2)) + align16((size_t)kJpTile * s.dim * u);
+    const size_t r4 = precision == EWALD_FP64 ? sizeof(Img64) : sizeof(float4);
+    return jp_coef_offset(n_g, s.dim, u) + 2 * (size_t)n_g * r4;
 }
 
 int launch_jastrow_p(const SysDev &s, const BatchDev &b, int precision, const JastrowDev &jd, double *j,
