@@ -4,7 +4,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The GPU library never imports it and
 the oracle imports nothing from the GPU library.
 
-Functions follow the paper's Sec. 2.2, Eqs. (2)-(6), and for the two-body
+Functions follow the paper's Sec. 2.2, Eqs. (2)-(6) (``energy_z`` and
+``delta_e_z``: 2D cells with charges at heights z != 0), and for the two-body
 plane-wave Jastrow term Sec. 2.3, Eqs. (7) and (9); see ``ewald_oracle.c`` for
 the formulas.  Every call takes positions as a ``(n, dim)`` float64 array
 of Cartesian coordinates and charges as an ``(n,)`` float64 array.
@@ -58,6 +59,10 @@ def _load():
             lib.oracle_cutoffs.argtypes = [c_int, c_double, c_double, dp, dp]
             lib.oracle_jastrow_stars.argtypes = [c_int, dp, c_int, c_int, ip, ip, ip]
             lib.oracle_jastrow_p.argtypes = [c_int, dp, c_int, dp, c_int, dp, dp, dp, dp]
+            lib.oracle_energy_z.argtypes = [dp, c_int, dp, dp, dp, c_double, c_double, c_double, dp, dp]
+            lib.oracle_delta_e_z.argtypes = [dp, c_int, dp, dp, dp, c_int, dp, c_double, c_double, c_double, dp]
+            lib.oracle_energy_z.restype = ctypes.c_int
+            lib.oracle_delta_e_z.restype = ctypes.c_int
             lib.oracle_jastrow_stars.restype = ctypes.c_int
             lib.oracle_jastrow_p.restype = ctypes.c_int
             for f in (lib.oracle_energy, lib.oracle_delta_e, lib.oracle_rho_at,
@@ -179,3 +184,34 @@ def jastrow_p(dim, lattice, pos, a):
     _check(_load().oracle_jastrow_p(dim, _dp(lat), n, _dp(pos), a.size, _dp(a), ctypes.byref(j), _dp(grad),
                                     _dp(lap)))
     return j.value, grad, lap
+
+
+def energy_z(lattice, pos, z, q, alpha, r_c, g_c):
+    """2D cell, charges at in-plane positions pos (n, 2) and heights z (n,):
+    (E, [E_real, E_madR, E_recip, E_self, E_bg]) from the pair definition."""
+    lat = _f64(lattice, (2, 2))
+    pos = _f64(pos)
+    n = pos.shape[0]
+    pos = pos.reshape(n, 2)
+    z = _f64(z, (n,))
+    q = _f64(q, (n,))
+    comp = np.zeros(5)
+    e = ctypes.c_double()
+    _check(_load().oracle_energy_z(_dp(lat), n, _dp(pos), _dp(z), _dp(q), alpha, r_c, g_c, _dp(comp),
+                                   ctypes.byref(e)))
+    return e.value, comp
+
+
+def delta_e_z(lattice, pos, z, q, k, r_new, alpha, r_c, g_c):
+    """Energy change when particle k moves in the plane to r_new (height unchanged)."""
+    lat = _f64(lattice, (2, 2))
+    pos = _f64(pos)
+    n = pos.shape[0]
+    pos = pos.reshape(n, 2)
+    z = _f64(z, (n,))
+    q = _f64(q, (n,))
+    rn = _f64(r_new, (2,))
+    de = ctypes.c_double()
+    _check(_load().oracle_delta_e_z(_dp(lat), n, _dp(pos), _dp(z), _dp(q), int(k), _dp(rn), alpha, r_c, g_c,
+                                    ctypes.byref(de)))
+    return de.value

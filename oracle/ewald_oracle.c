@@ -31,6 +31,9 @@
  * erfc terms of the reciprocal sum coincide and the bracket of v_E reduces
  * to 1/(alpha sqrt(pi)).
  *
+ * oracle_energy_z / oracle_delta_e_z (end of the file) take 2D cells whose
+ * charges sit at heights z != 0 (layers), from the pair definition.
+ *
  * The single-particle move (Sec. 2.1: VMC and DMC sampling keep asking for the
  * potential-energy change of a one-particle move) is computed by
  * oracle_delta_e straight from its definition, with its own rho(G).
@@ -589,4 +592,199 @@ int oracle_jastrow_p(int dim, const double *lattice, int n, const double *pos, i
     free(gs);
     free(ls);
     return st;
+}
+
+/* ===================================================================== */
+/*
+ * Two-dimensional cell with every charge at a height z above the plane
+ * (Sec. 2.2, Eqs. (5)-(6) with z != 0: layered systems such as bilayers).
+ * Positions are in-plane [n][2], heights z[n].  The energy is the pair sum
+ * of the definition, pair by pair:
+ *
+ *   V = sum_{i<j} q_i q_j v_E(rho_ij, z_ij) + 1/2 sum_j q_j^2 v_M
+ *
+ *   v_E(rho, z) = (pi/A) sum_{G != 0} F(G, z) e^{iG.rho}
+ *               + sum_R erfc(alpha |(rho + R, z)|) / |(rho + R, z)|
+ *               - (2 pi/A) [z erf(alpha z) + e^{-alpha^2 z^2} / (alpha sqrt(pi))]
+ *   F(G, z)     = [e^{zG} erfc(G/(2 alpha) + z alpha) + e^{-zG} erfc(G/(2 alpha) - z alpha)] / G
+ *   v_M         = Eq. (6), as in oracle_energy's 2D case.
+ *
+ * The five pieces returned (same order as oracle_energy):
+ *   E_real  = sum_{i<j} q_i q_j sum_R erfc(alpha r)/r,  r = |(rho_ij + R, z_ij)| < r_c
+ *   E_madR  = 1/2 sum q^2 sum_{R != 0, |R| < r_c} erfc(alpha R)/R
+ *   E_recip = (pi/A) sum_{G != 0, |G| <= g_c} [sum_{i<j} q_i q_j F(G, z_ij) cos(G.rho_ij)
+ *                                               + 1/2 sum_i q_i^2 F(G, 0)]
+ *   E_self  = -(alpha/sqrt(pi)) sum q^2
+ *   E_bg    = -(2 pi/A) [sum_{i<j} q_i q_j g(z_ij) + 1/2 sum_i q_i^2 g(0)],
+ *             g(z) = z erf(alpha z) + e^{-alpha^2 z^2} / (alpha sqrt(pi))
+ *
+ * (F(G, 0) = 2 erfc(G/2alpha)/G and g(0) = 1/(alpha sqrt(pi)) give v_M's
+ * reciprocal and background constants.)  With every z equal this is
+ * oracle_energy's 2D result.  F is evaluated as printed, which needs
+ * e^{|z|G} to stay finite: the call refuses |z_ij| g_c > 600.
+ *
+ * Parity status: pinned (reduction to the z = 0 energy, alpha independence
+ * with z != 0, the Fourier series of a charged sheet lattice for z != 0,
+ * the charged-sheet limit at large separation, invariances, move dE).
+ */
+static double parry_f(double g, double z, double alpha) {
+    z = fabs(z);
+    double a = g / (2.0 * alpha), b = z * alpha;
+    return (exp(z * g) * erfc(a + b) + exp(-z * g) * erfc(a - b)) / g;
+}
+
+static double sheet_g(double z, double alpha) {
+    return z * erf(alpha * z) + exp(-alpha * alpha * z * z) / (alpha * sqrt(M_PI));
+}
+
+/* Sum over in-plane lattice vectors R of erfc(alpha r)/r, r = |(d + R, z)| < r_c. */
+static int image_sum_z(const cell_t *c, const double *d, double z, double alpha, double r_c, double *out) {
+    double dw[3] = {0, 0, 0};
+    wrap(c, d, dw);
+    double dn = norm(2, dw);
+    int mmax[2];
+    for (int k = 0; k < 2; ++k) mmax[k] = (int)ceil((r_c + dn) * norm(2, c->b[k]) / (2.0 * M_PI));
+    double s = 0.0;
+    for (int m0 = -mmax[0]; m0 <= mmax[0]; ++m0)
+        for (int m1 = -mmax[1]; m1 <= mmax[1]; ++m1) {
+            double x0 = dw[0] + m0 * c->a[0][0] + m1 * c->a[1][0];
+            double x1 = dw[1] + m0 * c->a[0][1] + m1 * c->a[1][1];
+            double r = sqrt(x0 * x0 + x1 * x1 + z * z);
+            if (r < r_c) {
+                if (r < 1e-10 * sqrt(c->vol)) return ORC_ERR_COINCIDENT;
+                s += erfc(alpha * r) / r;
+            }
+        }
+    *out = s;
+    return ORC_OK;
+}
+
+typedef struct {
+    int n, k;          /* k >= 0: only pairs (k, j) for a move, with r_new */
+    const double *pos, *z, *q, *r_new;
+    double alpha;
+    ksum_t sum;
+} zrecip_ctx;
+
+/* sum_{i<j} q_i q_j F(G, z_ij) cos(G.rho_ij) + 1/2 sum q_i^2 F(G, 0) */
+static void visit_recip_z(const double *G, double g, const int *nvec, void *vctx) {
+    (void)nvec;
+    zrecip_ctx *r = (zrecip_ctx *)vctx;
+    double s = 0.0, f0 = parry_f(g, 0.0, r->alpha), zl = 0.0, fl = f0;
+    for (int i = 0; i < r->n; ++i) {
+        s += 0.5 * r->q[i] * r->q[i] * f0;
+        for (int j = i + 1; j < r->n; ++j) {
+            double z = r->z[i] - r->z[j];
+            if (z != zl) {  /* F of the last height difference is reused */
+                zl = z;
+                fl = parry_f(g, z, r->alpha);
+            }
+            double ph = G[0] * (r->pos[2 * i] - r->pos[2 * j]) + G[1] * (r->pos[2 * i + 1] - r->pos[2 * j + 1]);
+            s += r->q[i] * r->q[j] * fl * cos(ph);
+        }
+    }
+    kadd(&r->sum, s);
+}
+
+static int check_z(const double *lattice, int n, const double *pos, const double *z, const double *q,
+                   double alpha, double r_c, double g_c, double *zmax) {
+    int st = check_common(2, lattice, n, pos, q, alpha, r_c, g_c);
+    if (st) return st;
+    if (!z) return ORC_ERR_ARG;
+    double lo = z[0], hi = z[0];
+    for (int i = 0; i < n; ++i) {
+        if (!isfinite(z[i])) return ORC_ERR_ARG;
+        lo = fmin(lo, z[i]);
+        hi = fmax(hi, z[i]);
+    }
+    *zmax = hi - lo;
+    if (*zmax * g_c > 600.0) return ORC_ERR_ARG;
+    return ORC_OK;
+}
+
+int oracle_energy_z(const double *lattice, int n, const double *pos, const double *z, const double *q,
+                    double alpha, double r_c, double g_c, double *comp, double *e) {
+    double zmax;
+    int st = check_z(lattice, n, pos, z, q, alpha, r_c, g_c, &zmax);
+    if (st) return st;
+    cell_t c;
+    if ((st = make_cell(2, lattice, &c))) return st;
+
+    ksum_t real = {0.0, 0.0}, bg = {0.0, 0.0};
+    double q2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        q2 += q[i] * q[i];
+        for (int j = i + 1; j < n; ++j) {
+            double d[2] = {pos[2 * i] - pos[2 * j], pos[2 * i + 1] - pos[2 * j + 1]}, s;
+            if ((st = image_sum_z(&c, d, z[i] - z[j], alpha, r_c, &s))) return st;
+            kadd(&real, q[i] * q[j] * s);
+            kadd(&bg, q[i] * q[j] * sheet_g(z[i] - z[j], alpha));
+        }
+    }
+    double zero[3] = {0, 0, 0}, smad;
+    if ((st = image_sum(&c, zero, alpha, r_c, 1, &smad))) return st;
+
+    zrecip_ctx rc = {n, -1, pos, z, q, NULL, alpha, {0.0, 0.0}};
+    for_each_g(&c, g_c, visit_recip_z, &rc);
+
+    double pa = M_PI / c.vol;
+    double e_real = kval(&real);
+    double e_madR = 0.5 * q2 * smad;
+    double e_recip = pa * kval(&rc.sum);
+    double e_self = -alpha / sqrt(M_PI) * q2;
+    double e_bg = -2.0 * pa * (kval(&bg) + 0.5 * q2 * sheet_g(0.0, alpha));
+    if (comp) {
+        comp[0] = e_real;
+        comp[1] = e_madR;
+        comp[2] = e_recip;
+        comp[3] = e_self;
+        comp[4] = e_bg;
+    }
+    *e = e_real + e_madR + e_recip + e_self + e_bg;
+    return ORC_OK;
+}
+
+/* v_E of one pair without the height term (it does not change in a move):
+ * the image sum and (pi/A) sum_G F(G, z) cos(G.rho), for every G. */
+typedef struct {
+    double rho[2], z, alpha;
+    ksum_t sum;
+} zpair_ctx;
+
+static void visit_pair_z(const double *G, double g, const int *nvec, void *vctx) {
+    (void)nvec;
+    zpair_ctx *p = (zpair_ctx *)vctx;
+    kadd(&p->sum, parry_f(g, p->z, p->alpha) * cos(G[0] * p->rho[0] + G[1] * p->rho[1]));
+}
+
+/*
+ * Energy change when particle k moves in the plane to r_new (its height
+ * stays z[k]), straight from the pair definition:
+ *   dE = q_k sum_{j != k} q_j [v_E(r_new - rho_j, z_kj) - v_E(rho_k - rho_j, z_kj)].
+ * The height term of v_E depends on z_kj only and cancels.
+ */
+int oracle_delta_e_z(const double *lattice, int n, const double *pos, const double *z, const double *q, int k,
+                     const double *r_new, double alpha, double r_c, double g_c, double *de) {
+    double zmax;
+    int st = check_z(lattice, n, pos, z, q, alpha, r_c, g_c, &zmax);
+    if (st) return st;
+    if (k < 0 || k >= n || !r_new || !de) return ORC_ERR_ARG;
+    cell_t c;
+    if ((st = make_cell(2, lattice, &c))) return st;
+    ksum_t tot = {0.0, 0.0};
+    for (int j = 0; j < n; ++j) {
+        if (j == k) continue;
+        double v[2];
+        for (int which = 0; which < 2; ++which) {
+            const double *rk = which ? r_new : pos + 2 * k;
+            double d[2] = {rk[0] - pos[2 * j], rk[1] - pos[2 * j + 1]}, s;
+            if ((st = image_sum_z(&c, d, z[k] - z[j], alpha, r_c, &s))) return st;
+            zpair_ctx pc = {{d[0], d[1]}, z[k] - z[j], alpha, {0.0, 0.0}};
+            for_each_g(&c, g_c, visit_pair_z, &pc);
+            v[which] = s + M_PI / c.vol * kval(&pc.sum);
+        }
+        kadd(&tot, q[k] * q[j] * (v[1] - v[0]));
+    }
+    *de = kval(&tot);
+    return ORC_OK;
 }
