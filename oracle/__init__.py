@@ -6,7 +6,8 @@ the oracle imports nothing from the GPU library.
 
 Functions follow the paper's Sec. 2.2, Eqs. (2)-(6) (``energy_z`` and
 ``delta_e_z``: 2D cells with charges at heights z != 0), and for the two-body
-plane-wave Jastrow term Sec. 2.3, Eqs. (7) and (9); see ``ewald_oracle.c`` for
+plane-wave Jastrow term Sec. 2.3, Eqs. (7) and (9), and for the polynomial
+two-body term Eq. (8); see ``ewald_oracle.c`` for
 the formulas.  Every call takes positions as a ``(n, dim)`` float64 array
 of Cartesian coordinates and charges as an ``(n,)`` float64 array.
 """
@@ -63,6 +64,9 @@ def _load():
             lib.oracle_delta_e_z.argtypes = [dp, c_int, dp, dp, dp, c_int, dp, c_double, c_double, c_double, dp]
             lib.oracle_energy_z.restype = ctypes.c_int
             lib.oracle_delta_e_z.restype = ctypes.c_int
+            lib.oracle_jastrow_u.argtypes = [c_int, dp, c_int, dp, c_int, c_double, c_int, c_int, dp, dp, dp, dp,
+                                             dp]
+            lib.oracle_jastrow_u.restype = ctypes.c_int
             lib.oracle_jastrow_stars.restype = ctypes.c_int
             lib.oracle_jastrow_p.restype = ctypes.c_int
             for f in (lib.oracle_energy, lib.oracle_delta_e, lib.oracle_rho_at,
@@ -215,3 +219,23 @@ def delta_e_z(lattice, pos, z, q, k, r_new, alpha, r_c, g_c):
     _check(_load().oracle_delta_e_z(_dp(lat), n, _dp(pos), _dp(z), _dp(q), int(k), _dp(rn), alpha, r_c, g_c,
                                     ctypes.byref(de)))
     return de.value
+
+
+def jastrow_u(dim, lattice, pos, n_up, L, C, alpha_like, alpha_unlike):
+    """J_u = sum_{i<j} u(r_ij), u(r) = (r - L)^C sum_l alpha_l r^l (r < L), nearest images, like /
+    unlike spin coefficients (particles < n_up spin up); alpha[1] is replaced by its cusp value.
+    Returns (J_u, gradient (n, dim), Laplacian (n,))."""
+    lat = _f64(lattice, (dim, dim))
+    pos = _f64(pos)
+    n = pos.shape[0]
+    pos = pos.reshape(n, dim)
+    al = _f64(alpha_like).reshape(-1)
+    au = _f64(alpha_unlike).reshape(-1)
+    if al.size != au.size:
+        raise ValueError("coefficient sets of different length")
+    j = ctypes.c_double()
+    grad = np.zeros((n, dim))
+    lap = np.zeros(n)
+    _check(_load().oracle_jastrow_u(dim, _dp(lat), n, _dp(pos), int(n_up), float(L), int(C), al.size - 1, _dp(al),
+                                    _dp(au), ctypes.byref(j), _dp(grad), _dp(lap)))
+    return j.value, grad, lap

@@ -788,3 +788,121 @@ int oracle_delta_e_z(const double *lattice, int n, const double *pos, const doub
     *de = kval(&tot);
     return ORC_OK;
 }
+
+/* ===================================================================== */
+/*
+ * Two-body polynomial Jastrow term u (Sec. 2.3, Eq. (8)):
+ *
+ *   J_u = sum_{i<j} u_{s_i s_j}(r_ij),
+ *   u(r) = (r - L_u)^C sum_{l=0}^{N_u} alpha_l r^l  for r < L_u, 0 beyond,
+ *
+ * r_ij being the distance from i to the nearest image of j.  L_u must lie
+ * below half the shortest nonzero lattice vector, so at most one image of
+ * j is inside L_u; the sum below visits every image inside L_u, which is
+ * that definition.  Particles 0 .. n_up-1 have spin up, the others spin
+ * down; like spins take the coefficients alpha_like, unlike spins
+ * alpha_unlike.  alpha_1 of each set is not an input: the Kato cusp
+ * condition u'(0) = Gamma fixes it,
+ *
+ *   alpha_1 = Gamma / (-L_u)^C + C alpha_0 / L_u,
+ *
+ * Gamma = 1/2 (unlike spins) and 1/4 (like spins) in 3D, 1 and 1/3 in 2D.
+ * Gradient and Laplacian with respect to particle i's position:
+ *
+ *   grad_i = sum_{j != i} u'(r_ij) x_ij / r_ij,
+ *   lap_i  = sum_{j != i} [u''(r_ij) + (d - 1) u'(r_ij) / r_ij],
+ *
+ * with x_ij = r_i - (nearest image of r_j).  u' and u'' by the product
+ * rule on (r - L_u)^C P(r), each power sum written out term by term.
+ *
+ * Parity status: pinned (cusp value of u', vanishing of u and its first
+ * C - 1 derivatives at L_u, finite differences of J_u, a two-particle
+ * closed form, image and spin bookkeeping, invariances).
+ */
+static double cusp_alpha1(int dim, int like, double L, int C, double a0) {
+    double gamma = dim == 3 ? (like ? 0.25 : 0.5) : (like ? 1.0 / 3.0 : 1.0);
+    return gamma / pow(-L, C) + C * a0 / L;
+}
+
+/* u, u', u'' of one set at r < L (alpha[1] already the cusp value) */
+static void u_terms(double r, double L, int C, int n_u, const double *alpha, double *u, double *du, double *d2u) {
+    double P = 0.0, dP = 0.0, d2P = 0.0;
+    for (int l = 0; l <= n_u; ++l) {
+        P += alpha[l] * pow(r, l);
+        if (l >= 1) dP += l * alpha[l] * pow(r, l - 1);
+        if (l >= 2) d2P += l * (l - 1) * alpha[l] * pow(r, l - 2);
+    }
+    double t = r - L;
+    double tC = pow(t, C), tC1 = pow(t, C - 1), tC2 = C >= 2 ? pow(t, C - 2) : 0.0;
+    *u = tC * P;
+    *du = C * tC1 * P + tC * dP;
+    *d2u = C * (C - 1) * tC2 * P + 2.0 * C * tC1 * dP + tC * d2P;
+}
+
+int oracle_jastrow_u(int dim, const double *lattice, int n, const double *pos, int n_up, double L, int C, int n_u,
+                     const double *alpha_like, const double *alpha_unlike, double *j_out, double *grad, double *lap) {
+    cell_t c;
+    if (n < 1 || !pos || !alpha_like || !alpha_unlike || !j_out || n_up < 0 || n_up > n) return ORC_ERR_ARG;
+    if (C < 1 || C > 8 || n_u < 1 || n_u > 24 || !(L > 0.0)) return ORC_ERR_ARG;
+    int st = make_cell(dim, lattice, &c);
+    if (st) return st;
+    /* L below half of every nonzero lattice vector of a box of small vectors */
+    for (int m0 = -2; m0 <= 2; ++m0)
+        for (int m1 = -2; m1 <= 2; ++m1)
+            for (int m2 = (dim == 3 ? -2 : 0); m2 <= (dim == 3 ? 2 : 0); ++m2) {
+                if (!m0 && !m1 && !m2) continue;
+                double R[3] = {0, 0, 0};
+                for (int y = 0; y < dim; ++y) R[y] = m0 * c.a[0][y] + m1 * c.a[1][y] + (dim == 3 ? m2 * c.a[2][y] : 0);
+                if (!(2.0 * L < norm(dim, R))) return ORC_ERR_ARG;
+            }
+    double al[2][25];
+    for (int l = 0; l <= n_u; ++l) {
+        al[0][l] = alpha_unlike[l];
+        al[1][l] = alpha_like[l];
+    }
+    al[0][1] = cusp_alpha1(dim, 0, L, C, al[0][0]);
+    al[1][1] = cusp_alpha1(dim, 1, L, C, al[1][0]);
+    ksum_t js = {0.0, 0.0};
+    ksum_t *gs = (ksum_t *)calloc((size_t)n * dim, sizeof(ksum_t));
+    ksum_t *ls = (ksum_t *)calloc((size_t)n, sizeof(ksum_t));
+    for (int i = 0; i < n && !st; ++i)
+        for (int j = 0; j < n && !st; ++j) {
+            if (i == j) continue;
+            const int like = (i < n_up) == (j < n_up);
+            double d[3] = {0, 0, 0}, dw[3] = {0, 0, 0};
+            for (int y = 0; y < dim; ++y) d[y] = pos[i * dim + y] - pos[j * dim + y];
+            wrap(&c, d, dw);
+            int mmax[3] = {0, 0, 0};
+            for (int k = 0; k < dim; ++k)
+                mmax[k] = (int)ceil((L + norm(dim, dw)) * norm(dim, c.b[k]) / (2.0 * M_PI));
+            int m[3];
+            for (m[0] = -mmax[0]; m[0] <= mmax[0]; ++m[0])
+                for (m[1] = -mmax[1]; m[1] <= mmax[1]; ++m[1])
+                    for (m[2] = -mmax[2]; m[2] <= mmax[2]; ++m[2]) {
+                        double x[3] = {0, 0, 0};
+                        for (int y = 0; y < dim; ++y) {
+                            x[y] = dw[y];
+                            for (int k = 0; k < dim; ++k) x[y] += m[k] * c.a[k][y];
+                        }
+                        const double r = norm(dim, x);
+                        if (r >= L) continue;
+                        if (r < 1e-10 * pow(c.vol, 1.0 / dim)) {
+                            st = ORC_ERR_COINCIDENT;
+                            continue;
+                        }
+                        double u, du, d2u;
+                        u_terms(r, L, C, n_u, al[like], &u, &du, &d2u);
+                        if (i < j) kadd(&js, u);
+                        for (int y = 0; y < dim; ++y) kadd(&gs[i * dim + y], du * x[y] / r);
+                        kadd(&ls[i], d2u + (dim - 1) * du / r);
+                    }
+        }
+    if (!st) {
+        *j_out = kval(&js);
+        for (int k = 0; grad && k < n * dim; ++k) grad[k] = kval(&gs[k]);
+        for (int k = 0; lap && k < n; ++k) lap[k] = kval(&ls[k]);
+    }
+    free(gs);
+    free(ls);
+    return st;
+}
