@@ -505,7 +505,8 @@ def run_batched(stream, steps):
 
 
 def run_configs(stream, steps=3, moves=4):
-    """The other single-system workloads at their own sizes, each in both
+    """The other single-system workloads at their own sizes (with the 2D
+    electron-hole bilayer, charges at two heights), each in both
     precisions: walker energies/s, move dE/s (propose + accept rounds) and the
     mixed path's per-walker error against the FP64 path (floor as in the
     tests).  Device-resident inputs; every step re-evaluates the same
@@ -514,7 +515,7 @@ def run_configs(stream, steps=3, moves=4):
     import torch
     from paper_2507_02888_gb300 import ewald, inputs
     out = {}
-    for name in ["heg3d_sc_n54", "heg2d_hex_n338", "diamond_3x3x3"]:
+    for name in ["heg3d_sc_n54", "heg2d_hex_n338", "diamond_3x3x3", "ehbilayer2d_hex_n338"]:
         w = inputs.workload(name)
         W, N, dim = w["n_walkers"], w["n"], w["dim"]
         rng = np.random.default_rng(77)
@@ -526,6 +527,8 @@ def run_configs(stream, steps=3, moves=4):
         e_d = torch.empty(W, dtype=torch.float64, device="cuda")
         de_d = torch.empty(W, dtype=torch.float64, device="cuda")
         row, energies = {"walkers": W, "n": N, "n_fixed": len(w["fixed_q"]), "dim": dim}, {}
+        if "z" in w:
+            row["layers"] = int(len(set(w["z"])))
         for prec in ("mixed", "fp64"):
             ctx = ewald.context_for(w, precision=prec, stream=stream)
             b = ewald.Batch(ctx, W)

@@ -5,8 +5,9 @@
  * quantum Monte Carlo walkers and the energy change of single-particle moves
  * (Thorpe, Smith, Hasnip & Drummond, "Acceleration of the CASINO quantum
  * Monte Carlo software using GPUs and OpenACC": Sec. 2.2, Eqs. (2)-(4) in 3D
- * and Eqs. (5)-(6) in 2D with every charge in the plane z = 0; Sec. 2.1 for
- * the single-particle moves of VMC/DMC).
+ * and Eqs. (5)-(6) in 2D, with every charge in the plane z = 0 or, for
+ * layered cells, at up to EWALD_MAX_LAYERS heights; Sec. 2.1 for the
+ * single-particle moves of VMC/DMC).
  *
  * Conventions
  *   - alpha ("gamma" below) is the screening parameter of erfc(alpha r); it
@@ -74,7 +75,17 @@ typedef struct {
                                     add less than FP32 resolves; see ewald_get_info) */
     int precision;               /* ewald_precision */
     int resum_every;             /* accepted moves between rho(G) rebuilds; 0 -> 64 */
+    /* Layered 2D systems (paper Eqs. (5)-(6) with z != 0: bilayers, charges
+     * above or below the plane).  dim 2 only; NULL = every particle at z = 0.
+     * Particles with equal heights (exactly equal doubles) form a layer; at
+     * most EWALD_MAX_LAYERS distinct heights among all particles.  A move
+     * changes the in-plane position only: heights belong to the context.
+     * Height differences must keep |z_i - z_j| * g_cutoff <= 600. */
+    const double *mobile_z;      /* [n_mobile] host memory, or NULL */
+    const double *fixed_z;       /* [n_fixed] host memory, or NULL */
 } ewald_desc;
+
+#define EWALD_MAX_LAYERS 4
 
 /* Read-only facts about a context (for tests, manifests and tuning). */
 typedef struct {
@@ -89,8 +100,11 @@ typedef struct {
     int n_runs, run_len;  /* G rows split into runs of <= run_len consecutive n1 */
     double e_madelung;    /* 1/2 sum q^2 sum_{R!=0} erfc(alpha R)/R  (all charges) */
     double e_self;        /* -(alpha/sqrt(pi)) sum q^2                (all charges) */
-    double e_background;  /* -pi Q^2/(2 Omega alpha^2) (3D), -sqrt(pi) Q^2/(A alpha) (2D) */
+    double e_background;  /* -pi Q^2/(2 Omega alpha^2) (3D), -sqrt(pi) Q^2/(A alpha) (2D);
+                             layered 2D: -(pi/A) sum_{L,L'} Q_L Q_L' g(z_L - z_L'),
+                             g(z) = z erf(alpha z) + exp(-alpha^2 z^2)/(alpha sqrt(pi)) */
     double e_fixed_real;  /* real-space pair sum among fixed particles */
+    int n_layers;         /* distinct particle heights (1 unless the desc gave heights) */
 } ewald_info;
 
 /* Create a context: validates the description, builds the G list, the image
@@ -154,8 +168,10 @@ int ewald_propose_move(ewald_batch *b, const int *k, const double *r_new, double
 int ewald_accept_move(ewald_batch *b, const unsigned char *accept, int on_device);
 /* Rebuild rho(G) of every walker from its positions. */
 int ewald_resum(ewald_batch *b);
-/* rho(G) of every walker, rho_out[W][n_g_half][2] (re, im), G in the order
- * of ewald_get_gvectors; includes the fixed particles' contribution. */
+/* rho(G) of every walker, rho_out[W][n_layers][n_g_half][2] (re, im), G in
+ * the order of ewald_get_gvectors, layers in increasing height (n_layers = 1
+ * unless the context has heights); includes the fixed particles'
+ * contribution. */
 int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device);
 
 /* Batched form: walkers of several batches - of different systems (N,

@@ -156,6 +156,30 @@ int build_device(ewald_ctx *c) {
     s.e_self = t.e_self;
     s.e_bg = t.e_bg;
     s.e_II = t.e_II;
+    // layered 2D
+    s.n_layers = t.n_layers;
+    for (int L = 0; L <= EWALD_MAX_LAYERS; ++L) s.lay_start[L] = L < (int)t.lay_start.size() ? t.lay_start[L] : 0;
+    s.lay_start[0] = 0;
+    if (t.n_layers == 1) s.lay_start[1] = t.n_mob;
+    s.lay_idx = nullptr;
+    s.mob_layer = nullptr;
+    s.z_mob = s.z_fix = s.gwl_d = nullptr;
+    s.z_mob_f = s.z_fix_f = s.gwl_f = nullptr;
+    if (t.n_layers > 1) {
+        std::vector<unsigned char> ml(t.mob_layer.begin(), t.mob_layer.end());
+        std::vector<float> zmf(t.z_mob.begin(), t.z_mob.end()), gwlf(t.gwl.begin(), t.gwl.end());
+        std::vector<double> zf(t.z_fix);
+        if (zf.empty()) zf.push_back(0.0);
+        std::vector<float> zff(zf.begin(), zf.end());
+        if ((e = upload(o, (int **)&s.lay_idx, t.lay_idx.data(), t.lay_idx.size()))) return cuda_fail(c, e);
+        if ((e = upload(o, (unsigned char **)&s.mob_layer, ml.data(), ml.size()))) return cuda_fail(c, e);
+        if ((e = upload(o, (double **)&s.z_mob, t.z_mob.data(), t.z_mob.size()))) return cuda_fail(c, e);
+        if ((e = upload(o, (float **)&s.z_mob_f, zmf.data(), zmf.size()))) return cuda_fail(c, e);
+        if ((e = upload(o, (double **)&s.z_fix, zf.data(), zf.size()))) return cuda_fail(c, e);
+        if ((e = upload(o, (float **)&s.z_fix_f, zff.data(), zff.size()))) return cuda_fail(c, e);
+        if ((e = upload(o, (double **)&s.gwl_d, t.gwl.data(), t.gwl.size()))) return cuda_fail(c, e);
+        if ((e = upload(o, (float **)&s.gwl_f, gwlf.data(), gwlf.size()))) return cuda_fail(c, e);
+    }
     // pair tiles of 32 x S particles per side; the largest item count (S = 1)
     // sizes the batches' partial-sum buffers, so any tiling fits later
     int S = t.n_mob >= 128 ? 4 : (t.n_mob >= 64 ? 2 : 1);
@@ -473,6 +497,7 @@ int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
     i->e_self = t.e_self;
     i->e_background = t.e_bg;
     i->e_fixed_real = t.e_II;
+    i->n_layers = t.n_layers;
     return EWALD_OK;
 }
 
@@ -504,7 +529,7 @@ int ewald_batch_create(ewald_ctx *c, int W, ewald_batch **out) {
     const SysDev &s = c->s;
     BatchDev &d = b->b;
     d.W = W;
-    const size_t slots = (size_t)s.n_runs * s.run_len;
+    const size_t slots = (size_t)s.n_runs * s.run_len * s.n_layers;  // rho of every layer
     std::vector<void *> &o = b->dev;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (!e) e = x; };
@@ -523,7 +548,7 @@ int ewald_batch_create(ewald_ctx *c, int W, ewald_batch **out) {
     chk(dalloc(o, &b->d_rnew, (size_t)W * 3));
     chk(dalloc(o, &b->d_de, W));
     chk(dalloc(o, &b->d_acc, W));
-    size_t io = std::max({(size_t)W * s.n_mob * s.dim, (size_t)W * s.n_gh * 2, (size_t)W * 5});
+    size_t io = std::max({(size_t)W * s.n_mob * s.dim, (size_t)W * s.n_layers * s.n_gh * 2, (size_t)W * 5});
     b->d_io_bytes = io * sizeof(double);
     chk(dalloc(o, &b->d_io, io));
     if (!e) {
@@ -678,7 +703,7 @@ int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device) {
     int e = launch_rho_out(c->s, b->b, c->d_g2slot, dst, c->stream);
     if (e) return cuda_fail(c, (cudaError_t)e);
     if (on_device) return EWALD_OK;
-    return copy_out(b, rho_out, b->d_io, (size_t)b->b.W * c->s.n_gh * 2 * sizeof(double), 0);
+    return copy_out(b, rho_out, b->d_io, (size_t)b->b.W * c->s.n_layers * c->s.n_gh * 2 * sizeof(double), 0);
 }
 
 int ewald_set_timing(ewald_ctx *c, int enable) {

@@ -113,9 +113,10 @@ __device__ __forceinline__ void sfac_runs(const SfacTile<R> &t, int4 rn, int dir
 // A thread starts its run from the product of three buffered powers and
 // steps along n1 by one complex multiplication per G.  Tile sums are in R
 // and are added into FP64.
-template <typename R, int DIM>
-__device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, int te, bool write_energy,
-                          unsigned char *smem) {
+// LAYERED: a layered 2D cell, one pass per layer (sfac_item_layers).
+template <typename R, int DIM, bool LAYERED>
+__device__ __forceinline__ void sfac_item_body(const SysDev &s, const BatchDev &b, int w, int chunk, int te,
+                                               bool write_energy, unsigned char *smem) {
     using C = Cx<R>;
     const int W1 = 2 * s.n1max + 1, W2 = 2 * s.n2max + 1, W3 = DIM == 3 ? s.n3max + 1 : 0;
     Part<R> *tp = (Part<R> *)smem;
@@ -132,72 +133,94 @@ __device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, 
     const int4 rn = make_int4(rn0.x, rn0.y, rn0.z, rn0.w * dir);
     // runs are stored longest first, so lane 0 holds the warp's longest run
     const int wmax = __shfl_sync(0xffffffffu, rn.w, 0);
-    SlotSum<R> ax[kRunLen], ay[kRunLen];
-
-    for (int e0 = 0; e0 < s.n_mob; e0 += te) {
-        const int ne = min(te, s.n_mob - e0);
-        __syncthreads();  // the previous tile's tables are no longer read
-        for (int t = tid; t < ne; t += blockDim.x) tp[t] = load_mobile<R>(s, b, w, e0 + t, DIM);
-        __syncthreads();
-        // powers by repeated multiplication (Eq. (10))
-        for (int t = tid; t < ne * DIM; t += blockDim.x) {
-            const int e = t / DIM, k = t - e * DIM;
-            R sn, cs;
-            FP<R>::sincospi2(FP<R>::frac(tp[e].u[k]), &sn, &cs);
-            const C base = {cs, sn};
-            C p = {R(1), R(0)};
-            if (k < 2) {
-                const int nm = k == 0 ? s.n1max : s.n2max;
-                C *P = k == 0 ? P1 + (size_t)e * W1 : P2 + (size_t)e * W2;
-                P[nm] = p;
-                for (int n = 1; n <= nm; ++n) {
-                    p = cmul(p, base);
-                    P[nm + n] = p;
-                    P[nm - n] = {p.x, -p.y};
+    const int slots = s.n_runs * s.run_len;
+    double epart = 0;
+    // one pass per layer (a single pass unless the cell is layered 2D); each
+    // layer's rho goes to its own slots
+    const int nl = LAYERED ? s.n_layers : 1;
+    for (int L = 0; L < nl; ++L) {
+        SlotSum<R> ax[kRunLen], ay[kRunLen];
+        const int e_lo = nl > 1 ? s.lay_start[L] : 0, e_hi = nl > 1 ? s.lay_start[L + 1] : s.n_mob;
+        for (int e0 = e_lo; e0 < e_hi; e0 += te) {
+            const int ne = min(te, e_hi - e0);
+            __syncthreads();  // the previous tile's tables are no longer read
+            for (int t = tid; t < ne; t += blockDim.x)
+                tp[t] = load_mobile<R>(s, b, w, nl > 1 ? s.lay_idx[e0 + t] : e0 + t, DIM);
+            __syncthreads();
+            // powers by repeated multiplication (Eq. (10))
+            for (int t = tid; t < ne * DIM; t += blockDim.x) {
+                const int e = t / DIM, k = t - e * DIM;
+                R sn, cs;
+                FP<R>::sincospi2(FP<R>::frac(tp[e].u[k]), &sn, &cs);
+                const C base = {cs, sn};
+                C p = {R(1), R(0)};
+                if (k < 2) {
+                    const int nm = k == 0 ? s.n1max : s.n2max;
+                    C *P = k == 0 ? P1 + (size_t)e * W1 : P2 + (size_t)e * W2;
+                    P[nm] = p;
+                    for (int n = 1; n <= nm; ++n) {
+                        p = cmul(p, base);
+                        P[nm + n] = p;
+                        P[nm - n] = {p.x, -p.y};
+                    }
+                } else {
+                    C *P = P3 + (size_t)e * W3;
+                    P[0] = p;
+                    for (int n = 1; n < W3; ++n) {
+                        p = cmul(p, base);
+                        P[n] = p;
+                    }
                 }
-            } else {
-                C *P = P3 + (size_t)e * W3;
-                P[0] = p;
-                for (int n = 1; n < W3; ++n) {
-                    p = cmul(p, base);
-                    P[n] = p;
+            }
+            __syncthreads();
+            const SfacTile<R> tl{tp, P1, P2, P3, W1, W2, W3, s.n1max, s.n2max, ne};
+            switch (wmax) {  // uniform over the warp: the loop stops at the warp's longest run
+                case 8: sfac_runs<R, DIM, 8>(tl, rn, dir, ax, ay); break;
+                case 7: sfac_runs<R, DIM, 7>(tl, rn, dir, ax, ay); break;
+                case 6: sfac_runs<R, DIM, 6>(tl, rn, dir, ax, ay); break;
+                case 5: sfac_runs<R, DIM, 5>(tl, rn, dir, ax, ay); break;
+                case 4: sfac_runs<R, DIM, 4>(tl, rn, dir, ax, ay); break;
+                case 3: sfac_runs<R, DIM, 3>(tl, rn, dir, ax, ay); break;
+                case 2: sfac_runs<R, DIM, 2>(tl, rn, dir, ax, ay); break;
+                case 1: sfac_runs<R, DIM, 1>(tl, rn, dir, ax, ay); break;
+                default: break;
+            }
+        }
+        if (has) {
+            double2 *rho = b.rho + ((size_t)w * nl + L) * slots;
+            const double2 *rfix = s.rho_fix ? s.rho_fix + (size_t)L * slots : nullptr;
+#pragma unroll
+            for (int r = 0; r < kRunLen; ++r) {
+                if (r < s.run_len) {
+                    const int slot = r * s.n_runs + run;
+                    double2 v = make_double2(0.0, 0.0);
+                    if (r < rn.w) {
+                        v.x = ax[r].get();
+                        v.y = ay[r].get();
+                        if (rfix) {
+                            v.x += rfix[slot].x;
+                            v.y += rfix[slot].y;
+                        }
+                        if (nl == 1) epart += s.gw_d[slot] * (v.x * v.x + v.y * v.y);
+                    }
+                    rho[slot] = v;
                 }
             }
         }
-        __syncthreads();
-        const SfacTile<R> tl{tp, P1, P2, P3, W1, W2, W3, s.n1max, s.n2max, ne};
-        switch (wmax) {  // uniform over the warp: the loop stops at the warp's longest run
-            case 8: sfac_runs<R, DIM, 8>(tl, rn, dir, ax, ay); break;
-            case 7: sfac_runs<R, DIM, 7>(tl, rn, dir, ax, ay); break;
-            case 6: sfac_runs<R, DIM, 6>(tl, rn, dir, ax, ay); break;
-            case 5: sfac_runs<R, DIM, 5>(tl, rn, dir, ax, ay); break;
-            case 4: sfac_runs<R, DIM, 4>(tl, rn, dir, ax, ay); break;
-            case 3: sfac_runs<R, DIM, 3>(tl, rn, dir, ax, ay); break;
-            case 2: sfac_runs<R, DIM, 2>(tl, rn, dir, ax, ay); break;
-            case 1: sfac_runs<R, DIM, 1>(tl, rn, dir, ax, ay); break;
-            default: break;
-        }
     }
-
-    const int slots = s.n_runs * s.run_len;
-    double epart = 0;
-    if (has) {
-        double2 *rho = b.rho + (size_t)w * slots;
-#pragma unroll
-        for (int r = 0; r < kRunLen; ++r) {
-            if (r < s.run_len) {
-                const int slot = r * s.n_runs + run;
-                double2 v = make_double2(0.0, 0.0);
-                if (r < rn.w) {
-                    v.x = ax[r].get();
-                    v.y = ay[r].get();
-                    if (s.rho_fix) {
-                        v.x += s.rho_fix[slot].x;
-                        v.y += s.rho_fix[slot].y;
-                    }
-                    epart += s.gw_d[slot] * (v.x * v.x + v.y * v.y);
+    if (nl > 1 && has) {
+        // layered: sum_{L,L'} W_{LL'}(G) Re(rho_L conj(rho_L')) over this
+        // thread's slots, from the values it has just stored
+        const double2 *rho = b.rho + (size_t)w * nl * slots;
+        for (int r = 0; r < s.run_len && r < rn.w; ++r) {
+            const int slot = r * s.n_runs + run;
+            for (int L = 0; L < nl; ++L) {
+                const double2 a = rho[(size_t)L * slots + slot];
+                epart += s.gwl_d[((size_t)L * nl + L) * slots + slot] * (a.x * a.x + a.y * a.y);
+                for (int M = L + 1; M < nl; ++M) {
+                    const double2 c = rho[(size_t)M * slots + slot];
+                    epart += 2.0 * s.gwl_d[((size_t)L * nl + M) * slots + slot] * (a.x * c.x + a.y * c.y);
                 }
-                rho[slot] = v;
             }
         }
     }
@@ -205,6 +228,21 @@ __device__ void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, 
         double tot = block_sum(epart, red);
         if (tid == 0) b.part_recip[(size_t)w * s.n_gchunks + chunk] = tot;
     }
+}
+
+// The layered pass out of line: its extra loop and epilogue stay out of the
+// register allocation of the kernels' single-plane path.
+template <typename R, int DIM>
+__device__ __noinline__ void sfac_item_layers(const SysDev &s, const BatchDev &b, int w, int chunk, int te,
+                                              bool write_energy, unsigned char *smem) {
+    sfac_item_body<R, DIM, true>(s, b, w, chunk, te, write_energy, smem);
+}
+
+template <typename R, int DIM>
+__device__ inline void sfac_item(const SysDev &s, const BatchDev &b, int w, int chunk, int te, bool write_energy,
+                                 unsigned char *smem) {
+    if (DIM == 2 && s.n_layers > 1) sfac_item_layers<R, DIM>(s, b, w, chunk, te, write_energy, smem);
+    else sfac_item_body<R, DIM, false>(s, b, w, chunk, te, write_energy, smem);
 }
 
 // One CTA, any number of warps.  The tile pair's particles are staged in
@@ -293,7 +331,7 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
                         const Part<R> &pb = tj[c * 32 + jj];
                         const PairGeom<R, DIM> g = pair_geom<R, DIM>(s, pi, pb);
                         const int c0 = ims.cand[g.sc * s.cand_max];
-                        const R r2 = image_r2<DIM>(g.x, ims.img[c0]);
+                        const R r2 = image_r2<DIM>(g.x, ims.img[c0], g.z2);
                         const bool pass = r2 < (valid(jj) ? FP<R>::rc2(s) : R(0));
                         if (is_close_first<R, DIM>(s, r2, pass))
                             acc.add64(close_pair_term<DIM>(s, pi, pb, c0, (double)(R(1) * pi.q * pb.q), b.status));

@@ -96,10 +96,12 @@ __global__ void k_combine(SysDev s, BatchDev b) {
 }
 
 __global__ void k_rho_out(SysDev s, BatchDev b, const int *__restrict__ g2slot, double *__restrict__ out) {
+    // out[W][n_layers][n_gh]: t = (w * n_layers + L) * n_gh + g
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)b.W * s.n_gh) return;
-    int w = (int)(t / s.n_gh), g = (int)(t - (long long)w * s.n_gh);
-    double2 v = b.rho[(size_t)w * s.n_runs * s.run_len + g2slot[g]];
+    if (t >= (long long)b.W * s.n_layers * s.n_gh) return;
+    const long long wl = t / s.n_gh;
+    const int g = (int)(t - wl * s.n_gh);
+    double2 v = b.rho[(size_t)wl * s.n_runs * s.run_len + g2slot[g]];
     out[2 * t] = v.x;
     out[2 * t + 1] = v.y;
 }
@@ -211,7 +213,7 @@ int launch_combine(const SysDev &s, const BatchDev &b, cudaStream_t st) {
 }
 
 int launch_rho_out(const SysDev &s, const BatchDev &b, const int *g2slot, double *out, cudaStream_t st) {
-    long long n = (long long)b.W * s.n_gh;
+    long long n = (long long)b.W * s.n_layers * s.n_gh;
     k_rho_out<<<(int)((n + 255) / 256), 256, 0, st>>>(s, b, g2slot, out);
     return cudaGetLastError();
 }

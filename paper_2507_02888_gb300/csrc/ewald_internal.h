@@ -6,11 +6,14 @@
 //   runs     : G rows split into runs of <= run_len consecutive n1 walked away
 //              from the row's smallest |G| (int4: n1 start, n2, n3, dir * len)
 //   gw       : weight of every G slot, 2 C f(G) (0 for padding slots)
-//   rho_fix  : fixed particles' rho(G) per slot
+//   rho_fix  : fixed particles' rho(G) per layer and slot
+//   gwl      : layered 2D only: weight of Re(rho_L conj(rho_L')) per layer
+//              pair and slot, (pi/A) F(G, z_L - z_L') (paper Eq. (5) at z != 0)
 // and per walker batch:
 //   u        : [W][dim][stride] fixed-point fractional coordinates (uint64,
 //              2^64 = one lattice period); FP32 loops use the top 32 bits
-//   rho      : [W][run_len * n_runs] rho(G) (double2); slot = r * n_runs + run
+//   rho      : [W][n_layers][run_len * n_runs] rho(G) (double2);
+//              slot = r * n_runs + run
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -78,6 +81,15 @@ struct SysDev {
     const unsigned long long *fix_u;  // [dim][fix_stride]
     // constants (FP64)
     double e_madR, e_self, e_bg, e_II;
+    // layered 2D (n_layers > 1): heights, per-layer particle lists, weights
+    int n_layers;                          // 1: one plane (or 3D); the fields below are unused
+    int lay_start[EWALD_MAX_LAYERS + 1];   // mobile particles of layer L: lay_idx[lay_start[L] ..]
+    const int *lay_idx;                    // mobile particle indices grouped by layer
+    const unsigned char *mob_layer;        // [n_mob] layer of each mobile particle
+    const double *z_mob, *z_fix;           // heights
+    const float *z_mob_f, *z_fix_f;
+    const double *gwl_d;                   // [n_layers][n_layers][slots]
+    const float *gwl_f;
 };
 
 // Per-batch device state.
@@ -115,7 +127,12 @@ struct HostTables {
     int run_len = kRunLen;
     std::vector<double> gw;    // [run_len * n_runs]
     std::vector<int> g2slot;   // [n_gh]
-    std::vector<double> rho_fix;  // [slots][2]
+    std::vector<double> rho_fix;  // [n_layers][slots][2]
+    // layered 2D
+    int n_layers = 1;
+    std::vector<double> z_mob, z_fix, layer_z;  // heights; layer_z ascending
+    std::vector<int> mob_layer, fix_layer, lay_idx, lay_start;
+    std::vector<double> gwl;      // [n_layers][n_layers][slots]
     int n1max = 0, n2max = 0, n3max = 0;
     // constants
     double e_madR = 0, e_self = 0, e_bg = 0, e_II = 0;
@@ -125,6 +142,9 @@ struct HostTables {
 int build_tables(const ewald_desc *d, HostTables *t, std::string *why);
 int pick_subcells(HostTables *t, int max_bytes);
 int set_subcells(HostTables *t, int bits);
+double shortest_lattice_vector(const HostTables &t);
+int short_range_lists(const HostTables &t, double cutoff, int max_bits, std::vector<double> *img,
+                      std::vector<unsigned short> *cand, int *bits_out);
 size_t subcell_bytes(const HostTables &t, int bits);
 
 // kernels.cu launchers (return cudaError_t as int)

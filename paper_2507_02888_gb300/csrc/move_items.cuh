@@ -6,6 +6,10 @@
 //   dE = q_k sum_{j != k} q_j sum_R [phi(r' - r_j + R) - phi(r - r_j + R)]
 //      + sum_{G half} 2 C f(G) (2 Re(conj(rho) delta) + |delta|^2),
 //   delta(G) = q_k (e^{iG.r'} - e^{iG.r}),  phi(x) = erfc(alpha|x|)/|x|.
+//
+// Layered 2D cells (particle k in layer K, weights W_{LL'}(G) of
+// Re(rho_L conj(rho_L'))): the reciprocal part is
+//   sum_{G half} [2 sum_L' W_{KL'} Re(conj(rho_L') delta) + W_KK |delta|^2].
 #pragma once
 #include "device_common.cuh"
 
@@ -119,6 +123,25 @@ __device__ inline bool cart_to_fixed(const SysDev &s, const double *r, unsigned 
     return ok;
 }
 
+// This thread's share of the reciprocal dE in a layered cell (particle k of
+// layer K), out of line like the layered structure factor.
+template <typename R, int DIM>
+__device__ __noinline__ R layered_recip_delta(const SysDev &s, const BatchDev &b, int w, int k, R qk,
+                                              const MoveTables<R> &tab) {
+    const int slots = s.n_runs * s.run_len, nl = s.n_layers, K = s.mob_layer[k];
+    const double2 *rho = b.rho + (size_t)w * nl * slots;
+    R part = 0;
+    for_each_delta<R, DIM>(s, tab, qk, [&](int slot, Cx<R> d) {
+        R t = FP<R>::gwl(s, ((size_t)K * nl + K) * slots + slot) * (d.x * d.x + d.y * d.y);
+        for (int L = 0; L < nl; ++L) {
+            const double2 rv = rho[(size_t)L * slots + slot];
+            t += R(2) * FP<R>::gwl(s, ((size_t)K * nl + L) * slots + slot) * ((R)rv.x * d.x + (R)rv.y * d.y);
+        }
+        part += t;
+    });
+    return part;
+}
+
 // dE of moving particle k of walker w from pold to pnew (tables of m built
 // and images staged).  All threads call it; the result is valid in thread 0.
 template <typename R, int DIM>
@@ -144,21 +167,27 @@ __device__ double move_delta_e(const SysDev &s, const BatchDev &b, int w, int k,
     wq.drain(acc, FP<R>::term_consts(s), lane);
     double tot = acc.get();
     // reciprocal space
-    const double2 *rho = b.rho + (size_t)w * s.n_runs * s.run_len;
     R part = 0;
-    for_each_delta<R, DIM>(s, m.tab, pold.q, [&](int slot, Cx<R> d) {
-        const double2 rv = rho[slot];
-        const R rx = (R)rv.x, ry = (R)rv.y;
-        part += FP<R>::gw(s, slot) * (R(2) * (rx * d.x + ry * d.y) + d.x * d.x + d.y * d.y);
-    });
+    if (DIM == 2 && s.n_layers > 1) {
+        part = layered_recip_delta<R, DIM>(s, b, w, k, pold.q, m.tab);
+    } else {
+        const double2 *rho = b.rho + (size_t)w * s.n_runs * s.run_len;
+        for_each_delta<R, DIM>(s, m.tab, pold.q, [&](int slot, Cx<R> d) {
+            const double2 rv = rho[slot];
+            const R rx = (R)rv.x, ry = (R)rv.y;
+            part += FP<R>::gw(s, slot) * (R(2) * (rx * d.x + ry * d.y) + d.x * d.x + d.y * d.y);
+        });
+    }
     tot += (double)part;
     return block_sum(tot, m.red);
 }
 
-// rho(G) += delta(G) of walker w (tables of m built): the FP64 running sum.
+// rho(G) += delta(G) of walker w's particle k (tables of m built): the
+// FP64 running sum (of k's layer in a layered cell).
 template <typename R, int DIM>
-__device__ void move_apply_rho(const SysDev &s, const BatchDev &b, int w, R qk, MoveSmem<R> &m) {
-    double2 *rho = b.rho + (size_t)w * s.n_runs * s.run_len;
+__device__ void move_apply_rho(const SysDev &s, const BatchDev &b, int w, int k, R qk, MoveSmem<R> &m) {
+    const size_t slots = (size_t)s.n_runs * s.run_len;
+    double2 *rho = b.rho + ((size_t)w * s.n_layers + (s.n_layers > 1 ? s.mob_layer[k] : 0)) * slots;
     for_each_delta<R, DIM>(s, m.tab, qk, [&](int slot, Cx<R> d) {
         double2 rv = rho[slot];
         rv.x += (double)d.x;

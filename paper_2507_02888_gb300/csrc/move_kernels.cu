@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kMoveThreads)
         set_lo<R>(pnew, d, su_new[d]);
     }
     pold.q = pnew.q = FP<R>::q_mob(s, k);
+    pold.z = pnew.z = s.n_layers > 1 ? FP<R>::z_mob(s, k) : R(0);
     build_move_tables<R, DIM>(s, pold.u, pnew.u, m.tab);
     __syncthreads();
 
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kMoveThreads)
     pold.q = FP<R>::q_mob(s, k);
     build_move_tables<R, DIM>(s, pold.u, pnew.u, m.tab);
     __syncthreads();
-    move_apply_rho<R, DIM>(s, b, w, pold.q, m);
+    move_apply_rho<R, DIM>(s, b, w, k, pold.q, m);
     __syncthreads();
     if (tid < DIM) b.u[((size_t)w * DIM + tid) * s.mob_stride + k] = b.pend_u[(size_t)w * 3 + tid];
     if (tid == 0) {

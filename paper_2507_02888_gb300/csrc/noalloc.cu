@@ -51,7 +51,7 @@ static size_t carve(const SysDev &s, int W, unsigned char *base, BatchDev *b) {
         off += (bytes + 255) & ~(size_t)255;
         return p;
     };
-    const size_t slots = (size_t)s.n_runs * s.run_len;
+    const size_t slots = (size_t)s.n_runs * s.run_len * s.n_layers;  // rho of every layer
     b->W = W;
     b->status = (int *)take(sizeof(int));
     b->u = (unsigned long long *)take((size_t)W * s.dim * s.mob_stride * sizeof(unsigned long long));

@@ -102,7 +102,7 @@ int srv_cuda(ewald_server *s, cudaError_t e, const char *what) {
 // Device bytes a request needs (everything allocated at admission).
 size_t request_bytes(const ewald_ctx *c, int W) {
     const SysDev &s = c->s;
-    const size_t slots = (size_t)s.n_runs * s.run_len;
+    const size_t slots = (size_t)s.n_runs * s.run_len * s.n_layers;  // rho of every layer
     size_t b = 0;
     auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
     add((size_t)W * s.dim * s.mob_stride * 8);                  // u
@@ -204,7 +204,7 @@ int admit(ewald_server *s, Req &r) {
     auto chk = [&](cudaError_t x) { if (!e) e = x; };
     BatchDev &b = r.b;
     b.W = r.W;
-    const size_t slots = (size_t)sd.n_runs * sd.run_len;
+    const size_t slots = (size_t)sd.n_runs * sd.run_len * sd.n_layers;  // rho of every layer
     chk(aalloc(r, &b.u, (size_t)r.W * sd.dim * sd.mob_stride, st));
     chk(aalloc(r, &b.rho, (size_t)r.W * slots, st));
     chk(aalloc(r, &b.part_real, (size_t)r.W * std::max(c->max_items, sd.n_items), st));

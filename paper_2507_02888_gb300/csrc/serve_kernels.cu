@@ -117,14 +117,15 @@ __global__ void __launch_bounds__(kMoveThreads, kServeMinBlocks) k_serve_step(Se
             set_lo<R>(pnew, q, s_unew[q]);
         }
         pold.q = pnew.q = FP<R>::q_mob(ss, k);
+        pold.z = pnew.z = ss.n_layers > 1 ? FP<R>::z_mob(ss, k) : R(0);
         if (dim == 3) build_move_tables<R, 3>(ss, pold.u, pnew.u, m.tab);
         else build_move_tables<R, 2>(ss, pold.u, pnew.u, m.tab);
         __syncthreads();
         const double de = dim == 3 ? move_delta_e<R, 3>(ss, sl.b, w, k, pold, pnew, m)
                                    : move_delta_e<R, 2>(ss, sl.b, w, k, pold, pnew, m);
         if (s_acc) {  // uniform over the CTA
-            if (dim == 3) move_apply_rho<R, 3>(ss, sl.b, w, pold.q, m);
-            else move_apply_rho<R, 2>(ss, sl.b, w, pold.q, m);
+            if (dim == 3) move_apply_rho<R, 3>(ss, sl.b, w, k, pold.q, m);
+            else move_apply_rho<R, 2>(ss, sl.b, w, k, pold.q, m);
             __syncthreads();
             if (threadIdx.x < dim) sl.b.u[((size_t)w * dim + threadIdx.x) * ss.mob_stride + k] = s_unew[threadIdx.x];
             if (threadIdx.x == 0) {

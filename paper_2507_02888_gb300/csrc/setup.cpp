@@ -183,13 +183,13 @@ static void build_images(HostTables *t) {
 // Returns the longest list.  A displacement cell is the parallelepiped [-1/2 + s/M,
 // -1/2 + (s+1)/M) of fractional coordinates; every point in it is within
 // d_max / M of its centre, so R can contribute only if |c + R| < r_c + d_max/M.
-static int build_cand(const HostTables &t, int bits, std::vector<unsigned short> *cand,
-                      std::vector<int> *len) {
+static int cand_lists(const HostTables &t, const std::vector<double> &imgs, double cutoff, int bits,
+                      std::vector<unsigned short> *cand, std::vector<int> *len) {
     int dim = t.dim, M = 1 << bits, n_sub = 1;
     for (int k = 0; k < dim; ++k) n_sub *= M;
     double rad = max_wrapped_norm(t) / M;
-    double lim = (t.r_c + rad) * (1 + 1e-9);
-    int n_img = (int)t.img.size() / 3;
+    double lim = (cutoff + rad) * (1 + 1e-9);
+    int n_img = (int)imgs.size() / 3;
     std::vector<std::vector<unsigned short>> lists(n_sub);
     int longest = 0;
     for (int s = 0; s < n_sub; ++s) {
@@ -200,7 +200,7 @@ static int build_cand(const HostTables &t, int bits, std::vector<unsigned short>
         double dn = 1e300;
         for (int i = 0; i < n_img; ++i) {
             double x[3];
-            for (int y = 0; y < 3; ++y) x[y] = c[y] + t.img[3 * i + y];
+            for (int y = 0; y < 3; ++y) x[y] = c[y] + imgs[3 * i + y];
             const double r = norm_n(x, dim);
             if (r < lim) {
                 if (r < dn) dn = r, nearest = (int)lists[s].size();
@@ -223,6 +223,10 @@ static int build_cand(const HostTables &t, int bits, std::vector<unsigned short>
         }
     }
     return longest;
+}
+
+static int build_cand(const HostTables &t, int bits, std::vector<unsigned short> *cand, std::vector<int> *len) {
+    return cand_lists(t, t.img, t.r_c, bits, cand, len);
 }
 
 int set_subcells(HostTables *t, int bits) {
@@ -255,6 +259,40 @@ int pick_subcells(HostTables *t, int max_bytes) {
     t->sub_bits = best_bits;
     t->cand_max = build_cand(*t, best_bits, &t->cand, &t->cand_len);
     return best_bits;
+}
+
+// erfcx(x) = exp(x^2) erfc(x) for x >= 0: directly while exp(x^2) stays
+// finite, else the asymptotic series 1/(x sqrt(pi)) sum_k (-1)^k (2k-1)!! /
+// (2x^2)^k (Abramowitz & Stegun 7.1.23), whose terms at x >= 26 fall below
+// 1e-19 by k = 8.
+static double erfcx_pos(double x) {
+    if (x < 26.0) return std::exp(x * x) * std::erfc(x);
+    const double v = 1.0 / (2.0 * x * x);
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k <= 8; ++k) {
+        term *= -(2.0 * k - 1.0) * v;
+        sum += term;
+    }
+    return sum / (x * std::sqrt(kPi));
+}
+
+// F(G, z) of the 2D reciprocal sum at height difference z (paper Eq. (5)):
+// [e^{zG} erfc(G/2alpha + z alpha) + e^{-zG} erfc(G/2alpha - z alpha)] / G.
+// With a = G/2alpha and b = |z| alpha (zG = 2ab) each product is written
+// without the large factor e^{|z|G}: e^{-a^2-b^2} erfcx(a + b), and
+// e^{-a^2-b^2} erfcx(a - b) if a >= b, else e^{-|z|G} erfc(a - b).
+static double parry_f(double g, double z, double alpha) {
+    const double a = g / (2 * alpha), b = std::fabs(z) * alpha;
+    const double e = std::exp(-a * a - b * b);
+    const double t1 = e * erfcx_pos(a + b);
+    const double t2 = a >= b ? e * erfcx_pos(a - b) : std::exp(-std::fabs(z) * g) * std::erfc(a - b);
+    return (t1 + t2) / g;
+}
+
+// z erf(alpha z) + exp(-alpha^2 z^2) / (alpha sqrt(pi)): the G = 0 term of
+// paper Eq. (5) at height difference z (divided by -2 pi / A)
+static double sheet_g(double z, double alpha) {
+    return z * std::erf(alpha * z) + std::exp(-alpha * alpha * z * z) / (alpha * std::sqrt(kPi));
 }
 
 static void build_gvectors(HostTables *t) {
@@ -349,6 +387,29 @@ static void build_gvectors(HostTables *t) {
             for (int k = 0; k < dim; ++k) t->gn.push_back(n[k]);
         }
     }
+    // layered 2D: weight (pi/A) F(G, z_L - z_L') of Re(rho_L conj(rho_L')),
+    // every ordered layer pair (half-space: +G and -G give equal terms)
+    t->gwl.clear();
+    if (t->n_layers > 1) {
+        const int nl = t->n_layers;
+        t->gwl.assign((size_t)nl * nl * slots, 0.0);
+        for (int run = 0; run < n_runs; ++run) {
+            const int *rn = &t->runs[4 * run];
+            const int dir = rn[3] > 0 ? 1 : -1, len = std::abs(rn[3]);
+            for (int j = 0; j < len; ++j) {
+                int n[3] = {rn[0] + dir * j, rn[1], rn[2]};
+                double G[3] = {0, 0, 0};
+                for (int y = 0; y < dim; ++y)
+                    for (int k = 0; k < dim; ++k) G[y] += n[k] * t->B[k][y];
+                const double g = norm_n(G, dim);
+                const int slot = j * n_runs + run;
+                for (int L = 0; L < nl; ++L)
+                    for (int M = 0; M < nl; ++M)
+                        t->gwl[((size_t)L * nl + M) * slots + slot] =
+                            C * parry_f(g, t->layer_z[L] - t->layer_z[M], t->alpha);
+            }
+        }
+    }
 }
 
 static void build_constants(HostTables *t) {
@@ -359,6 +420,15 @@ static void build_constants(HostTables *t) {
     t->e_self = -t->alpha / std::sqrt(kPi) * q2;
     t->e_bg = dim == 3 ? -kPi * Q * Q / (2 * t->volume * t->alpha * t->alpha)
                        : -std::sqrt(kPi) * Q * Q / (t->volume * t->alpha);
+    if (t->n_layers > 1) {  // -(pi/A) sum_{L,L'} Q_L Q_L' g(z_L - z_L')
+        std::vector<double> QL(t->n_layers, 0.0);
+        for (int i = 0; i < t->n_mob; ++i) QL[t->mob_layer[i]] += t->q_mob[i];
+        for (int i = 0; i < t->n_fix; ++i) QL[t->fix_layer[i]] += t->q_fix[i];
+        double sg = 0;
+        for (int L = 0; L < t->n_layers; ++L)
+            for (int M = 0; M < t->n_layers; ++M) sg += QL[L] * QL[M] * sheet_g(t->layer_z[L] - t->layer_z[M], t->alpha);
+        t->e_bg = -kPi / t->volume * sg;
+    }
     // Madelung self-image sum over R != 0 inside r_c: the image list covers |R| < r_c.
     int n_img = (int)t->img.size() / 3;
     double smad = 0;
@@ -376,19 +446,21 @@ static void build_constants(HostTables *t) {
             cart_to_frac(*t, d, f);
             for (int k = 0; k < dim; ++k) f[k] -= std::floor(f[k] + 0.5);
             lat_to_cart(*t, f, dw);
+            const double dz = t->n_layers > 1 ? t->z_fix[I] - t->z_fix[J] : 0.0;
             double s = 0;
             for (int i = 0; i < n_img; ++i) {
                 double x[3];
                 for (int y = 0; y < 3; ++y) x[y] = dw[y] + t->img[3 * i + y];
-                double r = norm_n(x, dim);
+                double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + (dim == 3 ? x[2] * x[2] : dz * dz));
                 if (r < t->r_c && r > 0) s += std::erfc(t->alpha * r) / r;
             }
             eII += t->q_fix[I] * t->q_fix[J] * s;
         }
     t->e_II = eII;
-    // fixed particles' rho(G) per slot: sum_I q_I exp(2 pi i n . f_I)
+    // fixed particles' rho(G) per layer and slot: sum_I q_I exp(2 pi i n . f_I)
     int n_runs = (int)t->runs.size() / 4;
-    t->rho_fix.assign((size_t)n_runs * t->run_len * 2, 0.0);
+    const size_t slots = (size_t)n_runs * t->run_len;
+    t->rho_fix.assign((size_t)t->n_layers * slots * 2, 0.0);
     if (t->n_fix == 0) return;
     std::vector<double> fr(t->n_fix * 3, 0.0);
     for (int I = 0; I < t->n_fix; ++I) cart_to_frac(*t, &t->fix_pos[I * dim], &fr[3 * I]);
@@ -397,19 +469,112 @@ static void build_constants(HostTables *t) {
         const int dir = rn[3] > 0 ? 1 : -1, len = std::abs(rn[3]);
         for (int j = 0; j < len; ++j) {
             int n[3] = {rn[0] + dir * j, rn[1], rn[2]};
-            double re = 0, im = 0;
+            const size_t slot = (size_t)j * n_runs + run;
             for (int I = 0; I < t->n_fix; ++I) {
                 double ph = 0;
                 for (int k = 0; k < dim; ++k) ph += n[k] * fr[3 * I + k];
                 ph = 2 * kPi * (ph - std::floor(ph));
-                re += t->q_fix[I] * std::cos(ph);
-                im += t->q_fix[I] * std::sin(ph);
+                const size_t o = 2 * ((t->n_layers > 1 ? (size_t)t->fix_layer[I] * slots : 0) + slot);
+                t->rho_fix[o] += t->q_fix[I] * std::cos(ph);
+                t->rho_fix[o + 1] += t->q_fix[I] * std::sin(ph);
             }
-            int slot = j * n_runs + run;
-            t->rho_fix[2 * slot] = re;
-            t->rho_fix[2 * slot + 1] = im;
         }
     }
+}
+
+// Layers: the distinct heights among all particles, ascending.  One height
+// (or none given) keeps n_layers = 1 and the plain 2D form: only height
+// differences enter the energy.
+static int setup_layers(HostTables *t, const ewald_desc *d, std::string *why) {
+    t->n_layers = 1;
+    t->layer_z.clear();
+    t->z_mob.clear();
+    t->z_fix.clear();
+    t->mob_layer.clear();
+    t->fix_layer.clear();
+    t->lay_idx.clear();
+    t->lay_start.clear();
+    if (!d->mobile_z && !d->fixed_z) return EWALD_OK;
+    std::vector<double> zm(t->n_mob, 0.0), zf(t->n_fix, 0.0);
+    if (d->mobile_z) zm.assign(d->mobile_z, d->mobile_z + t->n_mob);
+    if (d->fixed_z && t->n_fix) zf.assign(d->fixed_z, d->fixed_z + t->n_fix);
+    std::vector<double> zs(zm);
+    zs.insert(zs.end(), zf.begin(), zf.end());
+    std::sort(zs.begin(), zs.end());
+    zs.erase(std::unique(zs.begin(), zs.end()), zs.end());
+    if (zs.size() == 1) return EWALD_OK;
+    if ((int)zs.size() > EWALD_MAX_LAYERS) {
+        *why = "more distinct particle heights than EWALD_MAX_LAYERS";
+        return EWALD_ERR_ARG;
+    }
+    t->n_layers = (int)zs.size();
+    t->layer_z = zs;
+    t->z_mob = zm;
+    t->z_fix = zf;
+    auto layer_of = [&](double z) { return (int)(std::lower_bound(zs.begin(), zs.end(), z) - zs.begin()); };
+    for (double z : zm) t->mob_layer.push_back(layer_of(z));
+    for (double z : zf) t->fix_layer.push_back(layer_of(z));
+    t->lay_start.assign(t->n_layers + 1, 0);
+    for (int L = 0; L < t->n_layers; ++L) {
+        t->lay_start[L] = (int)t->lay_idx.size();
+        for (int i = 0; i < t->n_mob; ++i)
+            if (t->mob_layer[i] == L) t->lay_idx.push_back(i);
+    }
+    t->lay_start[t->n_layers] = (int)t->lay_idx.size();
+    return EWALD_OK;
+}
+
+// Shortest nonzero lattice vector (small integer combinations of a reduced
+// basis reach it).
+double shortest_lattice_vector(const HostTables &t) {
+    double rmin = 1e300;
+    const int r3 = t.dim == 3 ? 3 : 0;
+    for (int m0 = -3; m0 <= 3; ++m0)
+        for (int m1 = -3; m1 <= 3; ++m1)
+            for (int m2 = -r3; m2 <= r3; ++m2) {
+                if (!m0 && !m1 && !m2) continue;
+                double m[3] = {(double)m0, (double)m1, (double)m2}, x[3];
+                lat_to_cart(t, m, x);
+                rmin = std::min(rmin, norm_n(x, t.dim));
+            }
+    return rmin;
+}
+
+// Images and displacement-cell candidate lists for a short cutoff (the
+// Jastrow u term): every lattice vector within cutoff + the longest wrapped
+// displacement, nearest first, and the lists for the cell count (2^bits per
+// axis, bits <= max_bits) with the shortest longest list.  Returns that
+// length; img is [n][3], cand [n_sub][cand_max] padded with index n.
+int short_range_lists(const HostTables &t, double cutoff, int max_bits, std::vector<double> *img,
+                      std::vector<unsigned short> *cand, int *bits_out) {
+    const int dim = t.dim;
+    const double reach = cutoff + max_wrapped_norm(t);
+    int mb[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) mb[k] = (int)std::ceil(reach * norm_n(t.B[k], dim) / (2 * kPi));
+    struct Img { double r, x[3]; };
+    std::vector<Img> v;
+    for (int m0 = -mb[0]; m0 <= mb[0]; ++m0)
+        for (int m1 = -mb[1]; m1 <= mb[1]; ++m1)
+            for (int m2 = -mb[2]; m2 <= mb[2]; ++m2) {
+                double m[3] = {(double)m0, (double)m1, (double)m2}, x[3];
+                lat_to_cart(t, m, x);
+                const double r = norm_n(x, dim);
+                if (r < reach * (1 + 1e-9)) v.push_back({r, {x[0], x[1], x[2]}});
+            }
+    std::sort(v.begin(), v.end(), [](const Img &a, const Img &b) { return a.r < b.r; });
+    img->clear();
+    for (auto &i : v) img->insert(img->end(), {i.x[0], i.x[1], i.x[2]});
+    int best = 1 << 30, best_bits = 0;
+    for (int b = 0; b <= max_bits; ++b) {
+        const int L = cand_lists(t, *img, cutoff, b, nullptr, nullptr);
+        if (L < best) {
+            best = L;
+            best_bits = b;
+        }
+    }
+    std::vector<int> len;
+    *bits_out = best_bits;
+    return cand_lists(t, *img, cutoff, best_bits, cand, &len);
 }
 
 int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
@@ -431,6 +596,12 @@ int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
         *why = "non-finite input";
         return EWALD_ERR_ARG;
     }
+    if ((d->mobile_z || d->fixed_z) && dim != 2) { *why = "particle heights need dim 2"; return EWALD_ERR_ARG; }
+    if ((d->mobile_z && !all_finite(d->mobile_z, d->n_mobile)) ||
+        (d->fixed_z && d->n_fixed && !all_finite(d->fixed_z, d->n_fixed))) {
+        *why = "non-finite height";
+        return EWALD_ERR_ARG;
+    }
     t->dim = dim;
     t->n_mob = d->n_mobile;
     t->n_fix = d->n_fixed;
@@ -441,6 +612,7 @@ int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
     t->fix_pos.assign(d->fixed_pos, d->fixed_pos + (size_t)d->n_fixed * dim);
     int st = setup_lattice(t, d->lattice, why);
     if (st) return st;
+    if ((st = setup_layers(t, d, why))) return st;
 
     // Cutoff tolerances.  The G side is 1e-16 in both precisions (the
     // reciprocal sum is cheap and sets the G count).  The real-space side is
@@ -475,6 +647,10 @@ int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
     double Lc = std::pow(t->volume, 1.0 / dim);
     if (t->r_c > 64 * Lc || t->g_c * Lc / (2 * kPi) > 256) {
         *why = "cutoff too large for the cell";
+        return EWALD_ERR_ARG;
+    }
+    if (t->n_layers > 1 && (t->layer_z.back() - t->layer_z.front()) * t->g_c > 600) {
+        *why = "layer separation too large for the G cutoff (|dz| g_c > 600)";
         return EWALD_ERR_ARG;
     }
     build_images(t);

@@ -33,7 +33,7 @@ class Desc(ctypes.Structure):
     _fields_ = [("dim", _c_int), ("lattice", _dp), ("n_mobile", _c_int), ("mobile_charge", _dp),
                 ("n_fixed", _c_int), ("fixed_pos", _dp), ("fixed_charge", _dp), ("gamma", _c_double),
                 ("g_cutoff", _c_double), ("r_cutoff", _c_double), ("precision", _c_int),
-                ("resum_every", _c_int)]
+                ("resum_every", _c_int), ("mobile_z", _dp), ("fixed_z", _dp)]
 
 
 class TuneResult(ctypes.Structure):
@@ -47,7 +47,7 @@ class Info(ctypes.Structure):
                 ("volume", _c_double), ("n_g_half", _c_int), ("n_images", _c_int),
                 ("subcell_bits", _c_int), ("pair_tile", _c_int), ("max_candidates", _c_int), ("n_runs", _c_int),
                 ("run_len", _c_int), ("e_madelung", _c_double), ("e_self", _c_double),
-                ("e_background", _c_double), ("e_fixed_real", _c_double)]
+                ("e_background", _c_double), ("e_fixed_real", _c_double), ("n_layers", _c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -160,7 +160,8 @@ class Context:
     """One periodic system: cell, charges, alpha, cutoffs and precision."""
 
     def __init__(self, dim, lattice, mobile_charge, fixed_pos=None, fixed_charge=None, alpha=0.0,
-                 g_cutoff=0.0, r_cutoff=0.0, precision="fp64", resum_every=0, stream=None):
+                 g_cutoff=0.0, r_cutoff=0.0, precision="fp64", resum_every=0, stream=None, mobile_z=None,
+                 fixed_z=None):
         lib = load()
         self.dim = int(dim)
         self._lat = _f64(lattice, self.dim * self.dim)
@@ -169,9 +170,14 @@ class Context:
         self._fp = _f64(fixed_pos if nf else np.zeros(1))
         self._fq = _f64(fixed_charge if nf else np.zeros(1))
         prec = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED}.get(precision, precision)
+        # heights of a layered 2D cell (None: every particle in the plane)
+        self._zm = None if mobile_z is None else _f64(mobile_z)
+        self._zf = None if fixed_z is None or nf == 0 else _f64(fixed_z)
         d = Desc(self.dim, self._lat.ctypes.data_as(_dp), len(self._qm), self._qm.ctypes.data_as(_dp),
                  nf, self._fp.ctypes.data_as(_dp), self._fq.ctypes.data_as(_dp), float(alpha),
-                 float(g_cutoff), float(r_cutoff), int(prec), int(resum_every))
+                 float(g_cutoff), float(r_cutoff), int(prec), int(resum_every),
+                 None if self._zm is None else self._zm.ctypes.data_as(_dp),
+                 None if self._zf is None else self._zf.ctypes.data_as(_dp))
         h = _vp()
         if stream is None:
             st = None
@@ -298,9 +304,11 @@ class Batch:
         _check(_lib.ewald_resum(self._h), self.ctx)
 
     def rho(self, out=None):
-        n = self.ctx.info()["n_g_half"]
+        """rho(G) [W][n_layers][n_g_half][2] (the layer axis has length 1 unless the cell is layered)."""
+        inf = self.ctx.info()
+        n = inf["n_g_half"]
         if out is None:
-            out = np.zeros((self.W, n, 2))
+            out = np.zeros((self.W, inf["n_layers"], n, 2))
         p, dev = _ptr(out)
         _check(_lib.ewald_batch_get_rho(self._h, p, dev), self.ctx)
         return out
@@ -384,6 +392,10 @@ def measure_peaks():
 def context_for(workload, precision="fp64", stream=None, **kw):
     """Context for a workload dict from paper_2507_02888_gb300.inputs."""
     w = workload
+    if "z" in w and "mobile_z" not in kw:
+        kw["mobile_z"] = w["z"]
+        if len(w["fixed_q"]) and "fixed_z" in w:
+            kw["fixed_z"] = w["fixed_z"]
     return Context(w["dim"], w["lattice"], w["q"], w["fixed_pos"] if len(w["fixed_q"]) else None,
                    w["fixed_q"] if len(w["fixed_q"]) else None, alpha=w["alpha"], precision=precision,
                    stream=stream, **kw)

@@ -145,7 +145,8 @@ def workload(name, n_walkers=None):
     """Return a dict describing a named synthetic workload.
 
     Keys: dim, lattice, n, q (mobile charges), fixed_pos, fixed_q, alpha,
-    n_walkers, pos (W, N, dim), tag, moves (n per walker), sigma.
+    n_walkers, pos (W, N, dim), tag, moves (n per walker), sigma; layered 2D
+    workloads add z (N,), each mobile particle's height above the plane.
 
     alpha values other than the sc cell's are chosen so that the number of
     reciprocal vectors inside the 1e-16 cutoff is about 4000 (3D) or about
@@ -184,6 +185,16 @@ def workload(name, n_walkers=None):
         d = dict(dim=3, lattice=lat, n=n, alpha=0.25207, moves=100, sigma=0.3)
         pos = scattered_positions(rng_for(tag), fpos, W, n, 0.8)
         q = -np.ones(n)
+    elif name == "ehbilayer2d_hex_n338":  # 2D electron-hole bilayer: 169 e (z = 0) + 169 h (z = 5), r_s = 5
+        tag, n, rs, sep = 4, 338, 5.0, 5.0
+        lat = hex_lattice(n // 2, rs)        # area 169 pi r_s^2: r_s = 5 in each layer
+        W = n_walkers or 2048
+        # about 1000 G vectors: N_G ~ g_c^2 A / (4 pi), g_c = 2 alpha erfc^-1(1e-16)
+        d = dict(dim=2, lattice=lat, n=n, alpha=0.0839, moves=100, sigma=1.5)
+        pos = uniform_positions(rng_for(tag), lat, W, n)
+        q = np.where(np.arange(n) < n // 2, -1.0, 1.0)
+        d["z"] = np.where(np.arange(n) < n // 2, 0.0, sep)
+        fpos, fq = np.zeros((0, 2)), np.zeros(0)
     elif name.startswith("heg3d_sc_n"):   # serving-mix sizes: sc cells at r_s = 2
         n = int(name[len("heg3d_sc_n"):])
         tag, rs = 10 + n, 2.0

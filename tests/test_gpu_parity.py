@@ -150,7 +150,7 @@ def test_rho_matches_oracle(ew, prec):
     for walker in range(2):
         p, q = all_particles(w, walker)
         ref = oracle.rho_at(3, w["lattice"], p, q, nv)
-        got = rho[walker, :, 0] + 1j * rho[walker, :, 1]
+        got = rho[walker, 0, :, 0] + 1j * rho[walker, 0, :, 1]
         assert np.max(np.abs(got - ref)) <= tol * np.sqrt(np.sum(q ** 2)), np.max(np.abs(got - ref))
     # half space: no G appears together with -G, and none is zero
     keys = {tuple(v) for v in nv}
