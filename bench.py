@@ -447,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
         result["configs"] = run_configs(stream)
     if not args.no_jastrow:
         result["jastrow_p"] = run_jastrow(stream, args.workload)
+        result["jastrow_u"] = run_jastrow_u(stream, args.workload)
     if not args.no_batched:
         result["batched"] = run_batched(stream, 5)
     if not args.no_serving:
@@ -597,6 +598,51 @@ def run_jastrow(stream, workload, n_stars=8, steps=3):
         t = ev[0].elapsed_time(ev[1]) / 1e3
         out[prec] = {"walker_evaluations_per_s": W * steps / t, "n_g_half": n_g,
                      "phase_evaluations_per_s": 2.0 * W * N * n_g * steps / t}
+        b.close()
+        ctx.close()
+    return out
+
+
+def run_jastrow_u(stream, workload, C=3, steps=3):
+    """Polynomial two-body Jastrow term u (Sec. 2.3, Eq. (8)) of every walker
+    with gradients and Laplacians, both precisions: walker evaluations/s and
+    pair evaluations/s (every ordered pair (i, j), j != i, is visited once;
+    those inside L_u are evaluated).  L_u = 0.99 of half the shortest lattice
+    vector, N_u = 8, half the electrons spin up."""
+    import itertools
+    import torch
+    from paper_2507_02888_gb300 import ewald, inputs
+    w = inputs.workload(workload)
+    W, N, dim = w["n_walkers"], w["n"], w["dim"]
+    lat = np.asarray(w["lattice"])
+    L = 0.99 * min(np.linalg.norm(np.array(m) @ lat)
+                   for m in itertools.product(range(-2, 3), repeat=dim) if any(m)) / 2
+    b_like = [0.3, 0.0, -0.2, 0.4, 0.1, -0.2, 0.3, -0.1, 0.05]
+    b_unlike = [0.55, 0.0, 0.3, -0.6, 0.5, 0.1, -0.1, 0.05, -0.02]
+    al = [c / L ** (l + C) for l, c in enumerate(b_like)]
+    au = [c / L ** (l + C) for l, c in enumerate(b_unlike)]
+    pos_d = torch.tensor(w["pos"], device="cuda")
+    j = torch.empty(W, dtype=torch.float64, device="cuda")
+    g = torch.empty((W, N, dim), dtype=torch.float64, device="cuda")
+    lap = torch.empty((W, N), dtype=torch.float64, device="cuda")
+    out = {"workload": workload, "walkers": W, "L_u": L, "C": C, "N_u": len(b_like) - 1}
+    for prec in ("mixed", "fp64"):
+        ctx = ewald.context_for(w, precision=prec, stream=stream)
+        ctx.set_jastrow_u(N // 2, L, C, al, au)
+        b = ewald.Batch(ctx, W)
+        b.set_positions(pos_d)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        n_steps = steps if prec == "mixed" else 1
+        with torch.cuda.stream(stream):
+            b.jastrow_u(j, g, lap)
+            ev[0].record(stream)
+            for _ in range(n_steps):
+                b.jastrow_u(j, g, lap)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+        t = ev[0].elapsed_time(ev[1]) / 1e3
+        out[prec] = {"walker_evaluations_per_s": W * n_steps / t,
+                     "pair_visits_per_s": float(W) * N * (N - 1) * n_steps / t}
         b.close()
         ctx.close()
     return out

@@ -293,11 +293,35 @@ int ewald_get_timing(ewald_ctx *ctx, double *ms, long long *launches);
  * j_out[W] and optionally grad_out[W][N][dim] = dJ_p/dr_i and
  * lap_out[W][N] = Laplacian of J_p with respect to r_i (either may be NULL);
  * all three on the device or on the host together (on_device).  Positions
- * are the batch's; phases are exact (fixed-point) in both precisions, sums
- * in FP64.  Errors: EWALD_ERR_STATE without positions or stars. */
+ * are the batch's; phases are exact (fixed-point) in both precisions;
+ * EWALD_FP64 sums in FP64, EWALD_MIXED in compensated FP32 with rho(G) and
+ * J_p in FP64.  Errors: EWALD_ERR_STATE without positions or stars. */
 int ewald_jastrow_p_set(ewald_ctx *ctx, int n_stars, const double *a);
 int ewald_jastrow_p_count(const ewald_ctx *ctx, int *n_g);
 int ewald_jastrow_p(ewald_batch *b, double *j_out, double *grad_out, double *lap_out, int on_device);
+
+/* Polynomial two-body Jastrow term (paper Sec. 2.3, Eqs. (7), (8)):
+ *   J_u = sum_{i<j} u(r_ij),  u(r) = (r - L_u)^C sum_{l=0}^{n_u} alpha_l r^l for r < L_u, 0 beyond,
+ * over the mobile particles of each walker, r_ij the nearest-image distance.
+ * Mobile particles 0 .. n_up-1 have spin up, the others spin down; pairs of
+ * like spins use alpha_like[0..n_u], unlike spins alpha_unlike[0..n_u]
+ * (host memory).  alpha_*[1] is ignored: the Kato cusp condition u'(0) =
+ * Gamma fixes alpha_1 = Gamma/(-L_u)^C + C alpha_0/L_u, Gamma = 1/4 (like)
+ * and 1/2 (unlike) in 3D, 1/3 and 1 in 2D.  Requirements: 0 <= n_up <=
+ * n_mobile, 1 <= C <= 8, 1 <= n_u <= 24, 0 < L_u < half the shortest
+ * lattice vector (EWALD_ERR_ARG otherwise).  ewald_jastrow_u_set stores
+ * the term on the context (replacing an earlier one; it synchronises the
+ * context's stream).  ewald_jastrow_u writes j_out[W] and optionally
+ * grad_out[W][N][dim] and lap_out[W][N] (the gradient and Laplacian with
+ * respect to each particle; either may be NULL), all on the device or all
+ * on the host (on_device).  EWALD_FP64: FP64 throughout; EWALD_MIXED: FP32
+ * terms in compensated FP32 sums, J_u added up in FP64.  Errors:
+ * EWALD_ERR_STATE without positions or without a u term; coincident
+ * particles set the batch's status (EWALD_ERR_COINCIDENT at the next
+ * synchronising call). */
+int ewald_jastrow_u_set(ewald_ctx *ctx, int n_up, double L_u, int C, int n_u, const double *alpha_like,
+                        const double *alpha_unlike);
+int ewald_jastrow_u(ewald_batch *b, double *j_out, double *grad_out, double *lap_out, int on_device);
 
 /* Measured arithmetic peaks of the current GPU, for the rooflines of the
  * ALU-bound kernels: FP32 FMA and FP64 FMA in TFLOP/s (2 flop per FMA) and

@@ -462,6 +462,7 @@ static void destroy_now(ewald_ctx *c) {
     collect_timers(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     free_all(c->dev);
+    free_all(c->ju_dev);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }

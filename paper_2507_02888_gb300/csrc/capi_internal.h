@@ -28,6 +28,10 @@ struct ewald_ctx {
     int jp_n_g = 0, jp_n_stars = 0;
     int4 *d_jp_nvec = nullptr;     // (n1, n2, n3, star)
     double4 *d_jp_gvec = nullptr;  // (Gx, Gy, Gz, a of its star)
+    // polynomial two-body Jastrow term (jastrow_u.cu)
+    bool ju_set = false;
+    ewald::JuDev ju{};
+    std::vector<void *> ju_dev;    // its device tables
     // kernel timers
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;

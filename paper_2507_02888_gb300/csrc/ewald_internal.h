@@ -167,6 +167,18 @@ int launch_propose(const SysDev &s, const BatchDev &b, int precision, const Laun
 int launch_accept(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg,
                   const unsigned char *acc, int resum_every, cudaStream_t st);
 
+// Polynomial two-body Jastrow term u (jastrow_u.cu): device tables.
+struct JuDev {
+    int n_up, C, n_u, sub_bits, cand_max, n_img;
+    double L, L2;
+    float L_f, L2_f;
+    const double *coef_d;  // [2][n_u + 1]: unlike, like spins (alpha_1 from the cusp)
+    const float *coef_f;
+    const Img64 *img_d;    // [n_img + 1], the last a far sentinel
+    const float4 *img_f;
+    const unsigned short *cand;  // [2^(sub_bits dim)][cand_max]
+};
+
 // Kernel ids of the per-context timers (ewald_get_timing).
 enum { KT_INGEST = 0, KT_SFAC, KT_REAL, KT_COMBINE, KT_PROPOSE, KT_ACCEPT, KT_RESUM, KT_COUNT };
 int launch_rho_out(const SysDev &s, const BatchDev &b, const int *g2slot, double *out,

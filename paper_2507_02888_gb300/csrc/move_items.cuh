@@ -187,7 +187,7 @@ __device__ double move_delta_e(const SysDev &s, const BatchDev &b, int w, int k,
 template <typename R, int DIM>
 __device__ void move_apply_rho(const SysDev &s, const BatchDev &b, int w, int k, R qk, MoveSmem<R> &m) {
     const size_t slots = (size_t)s.n_runs * s.run_len;
-    double2 *rho = b.rho + ((size_t)w * s.n_layers + (s.n_layers > 1 ? s.mob_layer[k] : 0)) * slots;
+    double2 *rho = b.rho + ((size_t)w * s.n_layers + (DIM == 2 && s.n_layers > 1 ? s.mob_layer[k] : 0)) * slots;
     for_each_delta<R, DIM>(s, m.tab, qk, [&](int slot, Cx<R> d) {
         double2 rv = rho[slot];
         rv.x += (double)d.x;

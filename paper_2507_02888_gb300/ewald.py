@@ -99,6 +99,8 @@ SIGNATURES = [
     ("ewald_jastrow_p_set", _c_int, [_vp, _c_int, _vp]),
     ("ewald_jastrow_p_count", _c_int, [_vp, ctypes.POINTER(_c_int)]),
     ("ewald_jastrow_p", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
+    ("ewald_jastrow_u_set", _c_int, [_vp, _c_int, _c_double, _c_int, _c_int, _vp, _vp]),
+    ("ewald_jastrow_u", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
 ]
 
 KERNELS = ["ingest", "sfac", "real", "combine", "propose", "accept", "resum"]
@@ -211,6 +213,16 @@ class Context:
         n = _c_int()
         _check(_lib.ewald_jastrow_p_count(self._h, ctypes.byref(n)), self)
         return n.value
+
+    def set_jastrow_u(self, n_up, L_u, C, alpha_like, alpha_unlike):
+        """Polynomial two-body Jastrow term: cutoff L_u, order C at the cutoff,
+        coefficients alpha_l (l = 0..N_u) for like and unlike spins; alpha[1]
+        is set by the cusp condition.  Mobile particles below n_up are spin up."""
+        al, au = _f64(alpha_like), _f64(alpha_unlike)
+        if al.size != au.size:
+            raise ValueError("coefficient sets of different length")
+        _check(_lib.ewald_jastrow_u_set(self._h, int(n_up), float(L_u), int(C), al.size - 1,
+                                        ctypes.c_void_p(al.ctypes.data), ctypes.c_void_p(au.ctypes.data)), self)
 
     def set_timing(self, enable=True):
         _check(_lib.ewald_set_timing(self._h, int(bool(enable))))
@@ -325,6 +337,20 @@ class Batch:
         pg = _ptr(grad)[0] if grad is not None else None
         pl = _ptr(lap)[0] if lap is not None else None
         _check(_lib.ewald_jastrow_p(self._h, pj, pg, pl, dev), self.ctx)
+        return j, grad, lap
+
+    def jastrow_u(self, j=None, grad=None, lap=None, derivatives=True):
+        """J_u per walker and (derivatives=True) its gradient [W][N][dim] and
+        Laplacian [W][N] per particle; host arrays unless device tensors are given."""
+        N, dim = self.ctx.n_mobile, self.ctx.dim
+        if j is None:
+            j = np.zeros(self.W)
+            if derivatives:
+                grad, lap = np.zeros((self.W, N, dim)), np.zeros((self.W, N))
+        pj, dev = _ptr(j)
+        pg = _ptr(grad)[0] if grad is not None else None
+        pl = _ptr(lap)[0] if lap is not None else None
+        _check(_lib.ewald_jastrow_u(self._h, pj, pg, pl, dev), self.ctx)
         return j, grad, lap
 
     def sync(self):
