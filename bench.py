@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-configs", action="store_true", help="skip the per-config table (c0, c2, c3)")
     p.add_argument("--no-jastrow", action="store_true", help="skip the two-body plane-wave Jastrow term")
+    p.add_argument("--no-tune-alpha", action="store_true", help="skip the measured alpha balancing leg")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-requests-fp64", type=int, default=120)
     return p.parse_args()
@@ -397,6 +398,33 @@ def run_ours(args, rank, world, local_rank):
         result["mixed_over_fp64"] = energies_per_s / result["fp64"]["value"]
         b.close()
         ctx.close()
+
+        # ---- alpha balanced by measurement (ewald_tune_alpha), both forms:
+        # the same energies (alpha independence) at the fastest split
+        if not args.no_tune_alpha:
+            tuned = {"note": "alpha from ewald_tune_alpha on a sample of the walkers; energies compared with "
+                             "the FP64 path at the workload's alpha"}
+            for prec, sample, steps in (("mixed", 256, 3), ("fp64", 32, 1)):
+                a_t, _ = ewald.tune_alpha(dim, w["lattice"], w["q"], w["pos"][:sample],
+                                          w["fixed_pos"] if len(w["fixed_q"]) else None,
+                                          w["fixed_q"] if len(w["fixed_q"]) else None, alpha=w["alpha"],
+                                          precision=prec, stream=stream)
+                ctx, b = make(prec, alpha=a_t)
+                it = ctx.info()
+                # with the same moves as the other legs, so that the energies are of the
+                # same (moved) configurations as e_fp64
+                t_e, _, t_t, _ = timed_steps(b, ctx, steps, 1, M)
+                t_e = max_over_ranks([t_e])[0]
+                rel_t = (e_d.cpu().numpy() - e_fp64) / floor
+                tuned[prec] = {"alpha": a_t, "alpha_over_workload": a_t / w["alpha"],
+                               "value": world * W * steps / (t_e / 1e3), "unit": "walker energies/s",
+                               "n_g_half": it["n_g_half"], "r_cutoff": it["r_cutoff"],
+                               "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 3)
+                                                        for k, v in t_t.items() if v[1]},
+                               "vs_fp64_at_workload_alpha_max": float(np.max(np.abs(rel_t)))}
+                b.close()
+                ctx.close()
+            result["tuned_alpha"] = tuned
 
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:

@@ -253,6 +253,23 @@ typedef struct {
 } ewald_tune_result;
 int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *res);
 
+/* Splitting parameter by measurement (alpha balancing).  alpha moves work
+ * between the real-space sum (~alpha^-3) and the reciprocal sum (~alpha^3)
+ * without changing the energy (paper Eq. (2): v_E does not depend on gamma,
+ * up to the cutoff tolerances); the best balance depends on the precision,
+ * the system and the GPU.  For desc (r_cutoff and g_cutoff must be <= 0:
+ * they follow alpha) this times the full energy of the sample pos
+ * [n_walkers][N][dim] (host memory, Cartesian) on trial contexts at alpha =
+ * a0 x {0.6 ... 2} around a0 (desc->gamma if > 0, else the balanced
+ * default), refines around the fastest, and returns it in *alpha_out and
+ * its time per walker (microseconds) in *us_per_walker (may be NULL).
+ * Trials the cell cannot take (cutoffs too large) are skipped.  Uses
+ * cuda_stream like ewald_create; synchronises it.  Errors: EWALD_ERR_ARG
+ * for bad arguments, the starting context's error, EWALD_ERR_CUDA if no
+ * trial could be timed (e.g. coincident particles in the sample). */
+int ewald_tune_alpha(const ewald_desc *desc, void *cuda_stream, int n_walkers, const double *pos, double *alpha_out,
+                     double *us_per_walker);
+
 /* Full energies without any device allocation at call time.  Meant for
  * callers that cannot call cudaMalloc while they compute (a host framework
  * that owns all device memory through its own pool, a CUDA-graph capture

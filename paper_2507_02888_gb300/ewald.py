@@ -101,6 +101,7 @@ SIGNATURES = [
     ("ewald_jastrow_p", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
     ("ewald_jastrow_u_set", _c_int, [_vp, _c_int, _c_double, _c_int, _c_int, _vp, _vp]),
     ("ewald_jastrow_u", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
+    ("ewald_tune_alpha", _c_int, [_vp, _vp, _c_int, _vp, _vp, _vp]),
 ]
 
 KERNELS = ["ingest", "sfac", "real", "combine", "propose", "accept", "resum"]
@@ -415,6 +416,31 @@ def measure_peaks():
     return {"fp32_tflops": a.value, "fp64_tflops": b.value, "rsqrt_tops": c.value}
 
 
+def tune_alpha(dim, lattice, mobile_charge, pos, fixed_pos=None, fixed_charge=None, alpha=0.0, precision="fp64",
+               stream=None, mobile_z=None, fixed_z=None):
+    """Fastest splitting parameter for this system and precision, timed on the
+    sample configurations pos [W][N][dim] (host): (alpha, microseconds per walker)."""
+    lib = load()
+    lat = _f64(lattice, int(dim) * int(dim))
+    qm = _f64(mobile_charge)
+    nf = 0 if fixed_charge is None else len(fixed_charge)
+    fp = _f64(fixed_pos if nf else np.zeros(1))
+    fq = _f64(fixed_charge if nf else np.zeros(1))
+    zm = None if mobile_z is None else _f64(mobile_z)
+    zf = None if fixed_z is None or nf == 0 else _f64(fixed_z)
+    prec = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED}.get(precision, precision)
+    d = Desc(int(dim), lat.ctypes.data_as(_dp), len(qm), qm.ctypes.data_as(_dp), nf, fp.ctypes.data_as(_dp),
+             fq.ctypes.data_as(_dp), float(alpha), 0.0, 0.0, int(prec), 0,
+             None if zm is None else zm.ctypes.data_as(_dp), None if zf is None else zf.ctypes.data_as(_dp))
+    p = _f64(pos)
+    W = p.size // (len(qm) * int(dim))
+    st = None if stream is None else (_vp(stream) if isinstance(stream, int) else _vp(stream.cuda_stream))
+    a, us = ctypes.c_double(), ctypes.c_double()
+    _check(lib.ewald_tune_alpha(ctypes.byref(d), st, W, ctypes.c_void_p(p.ctypes.data), ctypes.byref(a),
+                                ctypes.byref(us)))
+    return a.value, us.value
+
+
 def context_for(workload, precision="fp64", stream=None, **kw):
     """Context for a workload dict from paper_2507_02888_gb300.inputs."""
     w = workload
@@ -422,6 +448,7 @@ def context_for(workload, precision="fp64", stream=None, **kw):
         kw["mobile_z"] = w["z"]
         if len(w["fixed_q"]) and "fixed_z" in w:
             kw["fixed_z"] = w["fixed_z"]
+    alpha = kw.pop("alpha", w["alpha"])
     return Context(w["dim"], w["lattice"], w["q"], w["fixed_pos"] if len(w["fixed_q"]) else None,
-                   w["fixed_q"] if len(w["fixed_q"]) else None, alpha=w["alpha"], precision=precision,
+                   w["fixed_q"] if len(w["fixed_q"]) else None, alpha=alpha, precision=precision,
                    stream=stream, **kw)
