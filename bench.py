@@ -634,9 +634,9 @@ def run_jastrow(stream, workload, n_stars=8, steps=3):
 def run_jastrow_u(stream, workload, C=3, steps=3):
     """Polynomial two-body Jastrow term u (Sec. 2.3, Eq. (8)) of every walker
     with gradients and Laplacians, both precisions: walker evaluations/s and
-    pair evaluations/s (every ordered pair (i, j), j != i, is visited once;
-    those inside L_u are evaluated).  L_u = 0.99 of half the shortest lattice
-    vector, N_u = 8, half the electrons spin up."""
+    pairs/s (every unordered pair is visited once; those inside L_u are
+    evaluated).  L_u = 0.99 of half the shortest lattice vector, N_u = 8, half
+    the electrons spin up."""
     import itertools
     import torch
     from paper_2507_02888_gb300 import ewald, inputs
@@ -670,7 +670,7 @@ def run_jastrow_u(stream, workload, C=3, steps=3):
             torch.cuda.synchronize()
         t = ev[0].elapsed_time(ev[1]) / 1e3
         out[prec] = {"walker_evaluations_per_s": W * n_steps / t,
-                     "pair_visits_per_s": float(W) * N * (N - 1) * n_steps / t}
+                     "pairs_per_s": float(W) * N * (N - 1) / 2 * n_steps / t}
         b.close()
         ctx.close()
     return out

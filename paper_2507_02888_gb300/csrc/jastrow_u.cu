@@ -13,10 +13,10 @@
 // u'(0) = Gamma (Gamma = 1/4 like, 1/2 unlike in 3D; 1/3 and 1 in 2D).
 //
 // One CTA per walker: the walker's fixed-point coordinates are staged in
-// shared memory; each thread owns particles i and walks every j.  The
-// fixed-point difference selects a displacement cell whose short candidate
-// list holds the lattice vectors that can bring the pair inside L_u; the
-// nearest candidate decides.  u, u', u'' come from one Horner pass for P,
+// shared memory and every unordered pair is evaluated once (tile pairs,
+// below).  The fixed-point difference selects a displacement cell whose
+// short candidate list holds the lattice vectors that can bring the pair
+// inside L_u; the nearest candidate decides.  u, u', u'' come from one Horner pass for P,
 // P', P''/2 and the product rule on (r - L_u)^C P(r).
 #include <algorithm>
 #include <cmath>
@@ -50,6 +50,37 @@ __host__ __device__ inline size_t ju_off_pos(int n_u, int n_img, int n_sub, int 
     return align16(ju_off_cand(n_u, n_img) + (size_t)n_sub * cand_max * sizeof(unsigned short));
 }
 
+// Per-particle sums of one tile side in shared memory: gradient (DIM) and
+// Laplacian, with a Kahan compensation in the FP32 path.
+template <typename R>
+struct JuSums {
+    R *s, *c;  // [DIM + 1][n_pad] each (c unused in FP64)
+    int n_pad;
+    __device__ void add(int q, int p, double v) {
+        if constexpr (sizeof(R) == 4) {
+            float &S = s[q * n_pad + p], &C = c[q * n_pad + p];
+            const float y = (float)v - C, t = S + y;
+            C = (t - S) - y;
+            S = t;
+        } else {
+            s[q * n_pad + p] += v;
+        }
+    }
+    __device__ double get(int q, int p) const {
+        if constexpr (sizeof(R) == 4) return (double)s[q * n_pad + p] - (double)c[q * n_pad + p];
+        else return s[q * n_pad + p];
+    }
+};
+
+// One CTA per walker, 32-particle tiles.  Every unordered pair is evaluated
+// once: a warp takes a tile pair (A, B), lane l holds particle i = 32 A + l
+// and walks the 32 j of B; i's gradient and Laplacian stay in the lane's
+// registers, j's (the opposite gradient, the same Laplacian term) are summed
+// over the warp for each j and kept by lane j.  Tile pairs are scheduled in
+// rounds of disjoint pairs (a round-robin schedule), so no two warps touch a
+// tile's sums in one round; the diagonal tiles (A, A) form the last round,
+// with every ordered pair and i's side only.  Sums go to shared memory per
+// particle in a fixed order: the result does not depend on timing.
 template <typename R, int DIM>
 __global__ void __launch_bounds__(kJuThreads)
     k_jastrow_u(SysDev s, BatchDev b, JuDev ju, double *__restrict__ j_out, double *__restrict__ grad,
@@ -60,114 +91,188 @@ __global__ void __launch_bounds__(kJuThreads)
     using R4 = typename T::R4;
     extern __shared__ __align__(32) unsigned char smem[];
     __shared__ double red[kJuThreads / 32];
-    const int w = blockIdx.x, tid = threadIdx.x, N = s.n_mob;
+    const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int N = s.n_mob, nt = (N + 31) / 32, n_pad = nt * 32;
     const int n_sub = 1 << (ju.sub_bits * DIM), nc = ju.n_u + 1;
     R *cf = (R *)smem;
     R4 *im = (R4 *)(smem + ju_off_img(ju.n_u));
     unsigned short *cd = (unsigned short *)(smem + ju_off_cand(ju.n_u, ju.n_img));
-    U *up = (U *)(smem + ju_off_pos(ju.n_u, ju.n_img, n_sub, ju.cand_max));
+    const size_t off_pos = ju_off_pos(ju.n_u, ju.n_img, n_sub, ju.cand_max);
+    U *up = (U *)(smem + off_pos);
+    JuSums<R> sums;
+    sums.n_pad = n_pad;
+    sums.s = (R *)(smem + align16(off_pos + (size_t)n_pad * DIM * sizeof(U)));
+    sums.c = sums.s + (size_t)(DIM + 1) * n_pad;
     for (int t = tid; t < 2 * nc; t += blockDim.x) cf[t] = ju_coef<R>(ju)[t];
     for (int t = tid; t <= ju.n_img; t += blockDim.x) im[t] = ju_img<R>(ju)[t];
     for (int t = tid; t < n_sub * ju.cand_max; t += blockDim.x) cd[t] = ju.cand[t];
-    for (int t = tid; t < N * DIM; t += blockDim.x) {
+    for (int t = tid; t < n_pad * DIM; t += blockDim.x) {
         const int e = t / DIM, k = t - e * DIM;
-        up[t] = T::from64(b.u[((size_t)w * DIM + k) * s.mob_stride + e]);
+        up[t] = e < N ? T::from64(b.u[((size_t)w * DIM + k) * s.mob_stride + e]) : (U)0;
     }
+    for (int t = tid; t < (DIM + 1) * n_pad * (sizeof(R) == 4 ? 2 : 1); t += blockDim.x) sums.s[t] = R(0);
     __syncthreads();
     const R L = sizeof(R) == 4 ? (R)ju.L_f : (R)ju.L, L2 = sizeof(R) == 4 ? (R)ju.L2_f : (R)ju.L2;
     const R coin2 = T::coin2(s);
     const int C = ju.C;
-    double jsum = 0.0;
-    for (int i = tid; i < N; i += blockDim.x) {
-        U ui[DIM];
+
+    // pair (i, j): false if j's nearest image is not inside L; else u, the
+    // vector g = u'(r) (r_i - r_j) / r and the Laplacian term u'' + (d-1) u'/r
+    auto pair = [&](const U *ui, int i, int j, R &u, R *g, R &lt) -> bool {
+        I d[DIM];
+        int sc = 0;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) ui[k] = up[i * DIM + k];
-        const bool up_i = i < ju.n_up;
-        Acc<R> gs[DIM], ls, js;
-        for (int j = 0; j < N; ++j) {
-            if (j == i) continue;
-            // fixed-point difference, its displacement cell, Cartesian vector
-            I d[DIM];
-            int sc = 0;
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) {
-                d[k] = (I)(ui[k] - up[j * DIM + k]);
-                if (ju.sub_bits) {
-                    const U h = (U)d[k] + ((U)1 << (T::BITS - 1));
-                    sc |= (int)(h >> (T::BITS - ju.sub_bits)) << (k * ju.sub_bits);
-                }
+        for (int k = 0; k < DIM; ++k) {
+            d[k] = (I)(ui[k] - up[j * DIM + k]);
+            if (ju.sub_bits) {
+                const U h = (U)d[k] + ((U)1 << (T::BITS - 1));
+                sc |= (int)(h >> (T::BITS - ju.sub_bits)) << (k * ju.sub_bits);
             }
-            R x[DIM];
-#pragma unroll
-            for (int y = 0; y < DIM; ++y) {
-                R v = 0;
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) v = T::lat_lo(s, k, y, (R)d[k], v);
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) v = T::lat(s, k, y, (R)d[k], v);
-                x[y] = v;
-            }
-            // the nearest candidate image (the only one that can be inside L)
-            R r2 = R(1e30), xs[DIM];
-            for (int c = 0; c < ju.cand_max; ++c) {
-                const R4 Rv = im[cd[sc * ju.cand_max + c]];
-                const R y0 = x[0] + Rv.x, y1 = x[1] + Rv.y;
-                R rr = y0 * y0 + y1 * y1;
-                R y2 = 0;
-                if (DIM == 3) {
-                    y2 = x[DIM - 1] + Rv.z;
-                    rr += y2 * y2;
-                }
-                if (rr < r2) {
-                    r2 = rr;
-                    xs[0] = y0;
-                    xs[1] = y1;
-                    if (DIM == 3) xs[DIM - 1] = y2;
-                }
-            }
-            if (!(r2 < L2)) continue;
-            if (r2 < coin2) {  // two particles on top of each other: flag, skip
-                atomicOr(b.status, ST_COINCIDENT);
-                continue;
-            }
-            const R rinv = sizeof(R) == 4 ? (R)rsqrt_nr((float)r2) : R(1) / sqrt(r2);
-            const R r = r2 * rinv;
-            // P, P', P''/2 by Horner
-            const R *a = cf + ((up_i == (j < ju.n_up)) ? nc : 0);
-            R p = a[ju.n_u], p1 = 0, p2 = 0;
-            for (int l = ju.n_u - 1; l >= 0; --l) {
-                p2 = p2 * r + p1;
-                p1 = p1 * r + p;
-                p = p * r + a[l];
-            }
-            // (r - L)^(C-2), (r - L)^(C-1), (r - L)^C
-            const R t = r - L;
-            R tc2 = 1;
-            for (int k = 2; k < C; ++k) tc2 *= t;
-            const R tc1 = C >= 2 ? tc2 * t : R(1), tc = tc1 * t;
-            const R u = tc * p;
-            const R du = R(C) * tc1 * p + tc * p1;
-            const R d2u = (C >= 2 ? R(C * (C - 1)) * tc2 * p : R(0)) + R(2 * C) * tc1 * p1 + R(2) * tc * p2;
-            js.add(u);
-            const R gr = du * rinv;
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) gs[k].add(gr * xs[k]);
-            ls.add(d2u + R(DIM - 1) * gr);
         }
-        const size_t o = (size_t)w * N + i;
-        if (grad)
-            for (int k = 0; k < DIM; ++k) grad[o * DIM + k] = gs[k].get();
-        if (lap) lap[o] = ls.get();
-        jsum += js.get();
+        R x[DIM];
+#pragma unroll
+        for (int y = 0; y < DIM; ++y) {
+            R v = 0;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) v = T::lat_lo(s, k, y, (R)d[k], v);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) v = T::lat(s, k, y, (R)d[k], v);
+            x[y] = v;
+        }
+        // the nearest candidate image (the only one that can be inside L)
+        R r2 = R(1e30), xs[DIM];
+        for (int c = 0; c < ju.cand_max; ++c) {
+            const R4 Rv = im[cd[sc * ju.cand_max + c]];
+            const R y0 = x[0] + Rv.x, y1 = x[1] + Rv.y;
+            R rr = y0 * y0 + y1 * y1;
+            R y2 = 0;
+            if (DIM == 3) {
+                y2 = x[DIM - 1] + Rv.z;
+                rr += y2 * y2;
+            }
+            if (rr < r2) {
+                r2 = rr;
+                xs[0] = y0;
+                xs[1] = y1;
+                if (DIM == 3) xs[DIM - 1] = y2;
+            }
+        }
+        if (!(r2 < L2)) return false;
+        if (r2 < coin2) {  // two particles on top of each other: flag, skip
+            atomicOr(b.status, ST_COINCIDENT);
+            return false;
+        }
+        const R rinv = sizeof(R) == 4 ? (R)rsqrt_nr((float)r2) : R(1) / sqrt(r2);
+        const R r = r2 * rinv;
+        // P, P', P''/2 by Horner
+        const R *a = cf + (((i < ju.n_up) == (j < ju.n_up)) ? nc : 0);
+        R p = a[ju.n_u], p1 = 0, p2 = 0;
+        for (int l = ju.n_u - 1; l >= 0; --l) {
+            p2 = p2 * r + p1;
+            p1 = p1 * r + p;
+            p = p * r + a[l];
+        }
+        // (r - L)^(C-2), (r - L)^(C-1), (r - L)^C
+        const R t = r - L;
+        R tc2 = 1;
+        for (int k = 2; k < C; ++k) tc2 *= t;
+        const R tc1 = C >= 2 ? tc2 * t : R(1), tc = tc1 * t;
+        u = tc * p;
+        const R du = R(C) * tc1 * p + tc * p1;
+        const R d2u = (C >= 2 ? R(C * (C - 1)) * tc2 * p : R(0)) + R(2 * C) * tc1 * p1 + R(2) * tc * p2;
+        const R gr = du * rinv;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) g[k] = gr * xs[k];
+        lt = d2u + R(DIM - 1) * gr;
+        return true;
+    };
+
+    Acc<R> jacc;  // this lane's share of J
+    const int nt2 = nt + (nt & 1);  // round-robin over an even number of tiles (the extra one is a bye)
+    const int n_rounds = nt2 - 1;
+    for (int rnd = 0; rnd <= n_rounds; ++rnd) {
+        const bool diag = rnd == n_rounds;
+        const int n_jobs = diag ? nt : nt2 / 2;
+        for (int job = warp; job < n_jobs; job += nw) {
+            int A, B;
+            if (diag) {
+                A = B = job;
+            } else if (job == 0) {
+                A = rnd;
+                B = nt2 - 1;
+            } else {
+                A = (rnd + job) % (nt2 - 1);
+                B = (rnd - job + nt2 - 1) % (nt2 - 1);
+            }
+            if (A >= nt || B >= nt) continue;  // the bye
+            if (A > B) {
+                const int t = A;
+                A = B;
+                B = t;
+            }
+            const int i = A * 32 + lane;
+            const bool vi = i < N;
+            U ui[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) ui[k] = up[i * DIM + k];
+            Acc<R> gi[DIM], li, gj[DIM], lj;  // i's sums; lane jj keeps j = 32 B + jj's
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = B * 32 + jj;
+                if (j >= N) break;  // uniform over the warp
+                R u = 0, g[DIM], lt = 0;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) g[k] = 0;
+                const bool ok = vi && j != i && pair(ui, i, j, u, g, lt);
+                if (ok) {
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) gi[k].add(g[k]);
+                    li.add(lt);
+                    jacc.add(diag ? R(0.5) * u : u);
+                }
+                if (!diag) {  // j's side: -g and lt summed over the warp's i
+                    R v[DIM + 1];
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) v[k] = ok ? -g[k] : R(0);
+                    v[DIM] = ok ? lt : R(0);
+#pragma unroll
+                    for (int k = 0; k <= DIM; ++k) v[k] = warp_sum(v[k]);
+                    if (lane == jj) {
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) gj[k].add(v[k]);
+                        lj.add(v[DIM]);
+                    }
+                }
+            }
+            if (vi) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) sums.add(k, i, gi[k].get());
+                sums.add(DIM, i, li.get());
+            }
+            const int jl = B * 32 + lane;
+            if (!diag && jl < N) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) sums.add(k, jl, gj[k].get());
+                sums.add(DIM, jl, lj.get());
+            }
+        }
+        __syncthreads();  // the next round's pairs share tiles with this round's
     }
-    jsum = block_sum(0.5 * jsum, red);  // every pair was seen from both ends
+    for (int p = tid; p < N; p += blockDim.x) {
+        const size_t o = (size_t)w * N + p;
+        if (grad)
+            for (int k = 0; k < DIM; ++k) grad[o * DIM + k] = sums.get(k, p);
+        if (lap) lap[o] = sums.get(DIM, p);
+    }
+    const double jsum = block_sum(jacc.get(), red);
     if (tid == 0) j_out[w] = jsum;
 }
 
 static size_t ju_smem(const SysDev &s, const JuDev &ju, int precision) {
     const size_t u = precision == EWALD_FP64 ? sizeof(unsigned long long) : sizeof(unsigned int);
-    const int n_sub = 1 << (ju.sub_bits * s.dim);
-    return ju_off_pos(ju.n_u, ju.n_img, n_sub, ju.cand_max) + (size_t)s.n_mob * s.dim * u;
+    const size_t r = precision == EWALD_FP64 ? 8 : 2 * 4;  // a sum (and its compensation) per quantity
+    const int n_sub = 1 << (ju.sub_bits * s.dim), n_pad = (s.n_mob + 31) / 32 * 32;
+    return align16(ju_off_pos(ju.n_u, ju.n_img, n_sub, ju.cand_max) + (size_t)n_pad * s.dim * u) +
+           (size_t)(s.dim + 1) * n_pad * r;
 }
 
 int launch_jastrow_u(const SysDev &s, const BatchDev &b, int precision, const JuDev &ju, double *j, double *grad,
