@@ -44,8 +44,15 @@ typedef struct ewald_batch ewald_batch; /* W walkers of one system, state on the
 /* Arithmetic of the kernels (paper Sec. 6: single vs double precision).
  * EWALD_FP64: every kernel in FP64.
  * EWALD_MIXED: erfc, sin/cos and per-tile sums in FP32 with compensated
- * accumulation; per-walker reductions, rho(G) and constants in FP64. */
-typedef enum { EWALD_FP64 = 0, EWALD_MIXED = 1 } ewald_precision;
+ * accumulation; per-walker reductions, rho(G) and constants in FP64.
+ * EWALD_FP64_TIERED: FP64 results (the FP64 cutoffs and error bound) with
+ * the real-space sum split by term size: a pair image whose erfc(alpha r)
+ * is above 1e-7 is evaluated in FP64 from the exact fixed-point geometry
+ * and FP64 charges, the smaller ones (their FP32 error is below 1e-14 of
+ * the pair's 1/r) and the image tests in FP32.  Every other kernel
+ * (structure factor, moves, batched and serving forms) runs as EWALD_FP64;
+ * ewald_get_info reports this value. */
+typedef enum { EWALD_FP64 = 0, EWALD_MIXED = 1, EWALD_FP64_TIERED = 2 } ewald_precision;
 
 enum {
     EWALD_OK = 0,

@@ -98,14 +98,26 @@ int build_device(ewald_ctx *c) {
     s.coin2_f = (float)s.coin2;
     // close radius of the FP32 path (set-up: r_close)
     s.close2_f = (float)(t.r_close * t.r_close);
+    {   // tiered FP64: FP64 for images with erfc(alpha r) > kTierErfc
+        double x = 3.0;  // erfc(x) = kTierErfc by Newton steps on log erfc
+        for (int it = 0; it < 50; ++it) {
+            const double f = std::log(std::erfc(x)) - std::log(kTierErfc);
+            const double fp = -2.0 / std::sqrt(M_PI) * std::exp(-x * x) / std::erfc(x);
+            x -= f / fp;
+        }
+        const double rt = x / t.alpha;
+        s.tier2_f = t.tiered ? (float)(rt * rt) : 0.0f;
+    }
     cudaError_t e;
     // images
     int n_img = (int)t.img.size() / 3;
     std::vector<Img64> imd(n_img + 1);
-    std::vector<float4> imf(n_img + 1);
+    std::vector<float4> imf(n_img + 1), iml(n_img + 1, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int i = 0; i < n_img; ++i) {
         imd[i] = Img64{t.img[3 * i], t.img[3 * i + 1], t.img[3 * i + 2], 0.0};
         imf[i] = make_float4((float)t.img[3 * i], (float)t.img[3 * i + 1], (float)t.img[3 * i + 2], 0.f);
+        iml[i] = make_float4((float)(t.img[3 * i] - (double)imf[i].x), (float)(t.img[3 * i + 1] - (double)imf[i].y),
+                             (float)(t.img[3 * i + 2] - (double)imf[i].z), 0.f);
     }
     // sentinel that pads the candidate lists: |d + R|^2 ~ 3e36 never passes the cutoff
     imd[n_img] = Img64{1e18, 1e18, 1e18, 0.0};
@@ -113,6 +125,7 @@ int build_device(ewald_ctx *c) {
     s.n_img = n_img;
     if ((e = upload(o, (Img64 **)&s.img_d, imd.data(), imd.size()))) return cuda_fail(c, e);
     if ((e = upload(o, (float4 **)&s.img_f, imf.data(), imf.size()))) return cuda_fail(c, e);
+    if ((e = upload(o, (float4 **)&s.img_lo_f, iml.data(), iml.size()))) return cuda_fail(c, e);
     // reciprocal
     s.n_runs = (int)t.runs.size() / 4;
     s.run_len = t.run_len;
@@ -333,7 +346,7 @@ std::string tune_key(const ewald_ctx *c) {
     const HostTables &t = c->t;
     std::ostringstream k;
     k.precision(9);
-    k << "dim=" << t.dim << " n=" << t.n_mob << " nfix=" << t.n_fix << " prec=" << t.precision
+    k << "dim=" << t.dim << " n=" << t.n_mob << " nfix=" << t.n_fix << " prec=" << (t.tiered ? 2 : t.precision)
       << " alpha=" << t.alpha << " rc=" << t.r_c << " gc=" << t.g_c << " A=";
     for (int i = 0; i < t.dim; ++i)
         for (int j = 0; j < t.dim; ++j) k << t.A[i][j] << (i == t.dim - 1 && j == t.dim - 1 ? "" : ",");
@@ -482,7 +495,7 @@ int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
     i->dim = t.dim;
     i->n_mobile = t.n_mob;
     i->n_fixed = t.n_fix;
-    i->precision = t.precision;
+    i->precision = t.tiered ? EWALD_FP64_TIERED : t.precision;
     i->alpha = t.alpha;
     i->r_cutoff = t.r_c;
     i->g_cutoff = t.g_c;

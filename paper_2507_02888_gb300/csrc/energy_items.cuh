@@ -20,11 +20,13 @@ __host__ __device__ inline size_t sfac_bytes(const SysDev &s, int precision, int
     return align16(te * part) + align16((size_t)te * W * cx) + align16((threads / 32) * sizeof(double));
 }
 
-__host__ __device__ inline size_t real_work_bytes(const SysDev &s, int precision, int warps) {
-    size_t part = precision == EWALD_FP64 ? sizeof(Part<double>) : sizeof(Part<float>);
-    size_t qe = precision == EWALD_FP64 ? sizeof(QE<double>) : sizeof(QE<float>);
+// tiered: the FP32 tiles and queues of the mixed path plus the head queues
+__host__ __device__ inline size_t real_work_bytes(const SysDev &s, int precision, int warps, bool tiered = false) {
+    size_t part = precision == EWALD_FP64 && !tiered ? sizeof(Part<double>) : sizeof(Part<float>);
+    size_t qe = precision == EWALD_FP64 && !tiered ? sizeof(QE<double>) : sizeof(QE<float>);
     return 2 * align16(s.tile * part) + align16((size_t)warps * kQueueCap * qe) +
-           align16((size_t)warps * kCloseCap * sizeof(unsigned)) + align16(kRealUnits * sizeof(double));
+           align16((size_t)warps * kCloseCap * sizeof(unsigned)) + align16(kRealUnits * sizeof(double)) +
+           (tiered ? align16((size_t)warps * kHeadCap * sizeof(uint2)) : 0);
 }
 
 // Tables of one electron tile in shared memory (see sfac_item).
@@ -255,9 +257,11 @@ __device__ inline void sfac_item(const SysDev &s, const BatchDev &b, int w, int 
 // partial sum depends on jsplit but not on how many warps the CTA has.
 // ims must already hold this system's images; work is this item's scratch
 // (its reduction array holds kRealUnits doubles: nst * jsplit must fit).
-template <typename R, int DIM>
+// TIER (R = float only): the tiered FP64 form, head terms in FP64 (see
+// pair_images_tiered); close pairs are head terms there.
+template <typename R, int DIM, bool TIER = false>
 __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, const ImageSmem<R> &ims,
-                          unsigned char *work, int jsplit = 1) {
+                          unsigned char *work, int jsplit = 1, const float4 *img_lo = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     size_t off = 0;
     Part<R> *ti = (Part<R> *)(work + off);
@@ -269,6 +273,8 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
     unsigned *cbase = (unsigned *)(work + off);
     off += align16((size_t)nw * kCloseCap * sizeof(unsigned));
     double *red = (double *)(work + off);
+    off += align16(kRealUnits * sizeof(double));
+    uint2 *hbase = (uint2 *)(work + off);  // head queues (TIER only)
 
     const int S = s.tile / 32;
     const int2 tt = s.items[p];
@@ -308,13 +314,26 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
         auto valid = [&](int jj) { return vi && (j0 + c * 32 + jj < nj) && (!(diag && a == c) || lane < jj); };
         Acc<R> acc;
         CloseList cl{cbase + warp * kCloseCap, 0};
-        for (int jj = j_lo; jj < j_lo + jlen; ++jj) {
-            const int lj = c * 32 + jj;
-            pair_images<R, DIM, true>(s, pi, tj[lj], valid(jj), R(1), ims.img, ims.cand, wq, acc, lane, &cl,
-                                      ((unsigned)li << 16) | (unsigned)lj);
+        if constexpr (TIER) {
+            HeadQueue hq{hbase + warp * kHeadCap, 0};
+            for (int jj = j_lo; jj < j_lo + jlen; ++jj) {
+                const int lj = c * 32 + jj;
+                pair_images_tiered<DIM>(s, pi, tj[lj], valid(jj), ims.img, img_lo, ims.cand, wq, hq, acc, lane,
+                                        ((unsigned)li << 16) | (unsigned)lj, ti, tj, i0, j0, fixedj);
+            }
+            wq.drain(acc, tk, lane);
+            __syncwarp();
+            if (lane < hq.n) acc.add64(head_term<DIM>(s, ti, tj, i0, j0, fixedj, hq.q[lane], b.status));
+            __syncwarp();
+        } else {
+            for (int jj = j_lo; jj < j_lo + jlen; ++jj) {
+                const int lj = c * 32 + jj;
+                pair_images<R, DIM, true>(s, pi, tj[lj], valid(jj), R(1), ims.img, ims.cand, wq, acc, lane, &cl,
+                                          ((unsigned)li << 16) | (unsigned)lj);
+            }
+            wq.drain(acc, tk, lane);
         }
-        wq.drain(acc, tk, lane);
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (sizeof(R) == 4 && !TIER) {
             if (cl.n > 0) {  // uniform over the warp; close pairs are rare
                 __syncwarp();
                 if (cl.n <= kCloseCap) {

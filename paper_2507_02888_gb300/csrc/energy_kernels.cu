@@ -89,6 +89,23 @@ __global__ void __launch_bounds__(kRealThreads, sizeof(R) == 4 ? kRealMinBlocks3
     }
 }
 
+// Tiered FP64 form: FP32 tiles and image tests, head terms in FP64.
+template <int DIM>
+__global__ void __launch_bounds__(kRealThreads, kRealMinBlocks64) k_real_tiered(SysDev s, BatchDev b) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    ImageSmem<float> ims;
+    ims.carve(smem, s, DIM);
+    ims.stage(s, DIM);
+    float4 *img_lo = (float4 *)(smem + ImageSmem<float>::bytes(s, DIM));
+    for (int i = threadIdx.x; i <= s.n_img; i += blockDim.x) img_lo[i] = s.img_lo_f[i];
+    unsigned char *work = smem + ImageSmem<float>::bytes(s, DIM) + align16((s.n_img + 1) * sizeof(float4));
+    const long long total = (long long)b.W * s.n_items;
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        const int w = (int)(item / s.n_items), p = (int)(item - (long long)w * s.n_items);
+        real_item<float, DIM, true>(s, b, w, p, ims, work, 1, img_lo);
+    }
+}
+
 // ----------------------------------------------------------------- combine
 __global__ void k_combine(SysDev s, BatchDev b) {
     int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -110,6 +127,9 @@ __global__ void k_rho_out(SysDev s, BatchDev b, const int *__restrict__ g2slot, 
 static size_t sfac_smem(const SysDev &s, int precision, int te) { return sfac_bytes(s, precision, te, kSfacThreads); }
 
 static size_t real_smem(const SysDev &s, int precision) {
+    if (s.tier2_f > 0)
+        return ImageSmem<float>::bytes(s, s.dim) + align16((s.n_img + 1) * sizeof(float4)) +
+               real_work_bytes(s, precision, kRealWarps, true);
     size_t img = precision == EWALD_FP64 ? ImageSmem<double>::bytes(s, s.dim) : ImageSmem<float>::bytes(s, s.dim);
     return img + real_work_bytes(s, precision, kRealWarps);
 }
@@ -136,7 +156,17 @@ int configure_launch(SysDev &s, int precision, LaunchCfg *cfg) {
     cfg->sfac_smem = sfac_smem(s, precision, te);
     cfg->real_smem = real_smem(s, precision);
     int occ = 0;
-    if (precision == EWALD_FP64) {
+    if (s.tier2_f > 0) {  // tiered FP64: FP64 structure factor, tiered real space
+        if (s.dim == 3) {
+            if ((e = allow_smem(k_sfac<double, 3>, cfg->sfac_smem))) return e;
+            if ((e = allow_smem(k_real_tiered<3>, cfg->real_smem))) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_real_tiered<3>, kRealThreads, cfg->real_smem);
+        } else {
+            if ((e = allow_smem(k_sfac<double, 2>, cfg->sfac_smem))) return e;
+            if ((e = allow_smem(k_real_tiered<2>, cfg->real_smem))) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_real_tiered<2>, kRealThreads, cfg->real_smem);
+        }
+    } else if (precision == EWALD_FP64) {
         if (s.dim == 3) {
             if ((e = allow_smem(k_sfac<double, 3>, cfg->sfac_smem))) return e;
             if ((e = allow_smem(k_real<double, 3>, cfg->real_smem))) return e;
@@ -197,7 +227,10 @@ int launch_sfac(const SysDev &s, const BatchDev &b, int precision, const LaunchC
 int launch_real(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg, cudaStream_t st) {
     long long total = (long long)b.W * s.n_items;
     int grid = (int)std::min<long long>(total, cfg.real_grid);
-    if (precision == EWALD_FP64) {
+    if (s.tier2_f > 0) {
+        if (s.dim == 3) k_real_tiered<3><<<grid, kRealThreads, cfg.real_smem, st>>>(s, b);
+        else k_real_tiered<2><<<grid, kRealThreads, cfg.real_smem, st>>>(s, b);
+    } else if (precision == EWALD_FP64) {
         if (s.dim == 3) k_real<double, 3><<<grid, kRealThreads, cfg.real_smem, st>>>(s, b);
         else k_real<double, 2><<<grid, kRealThreads, cfg.real_smem, st>>>(s, b);
     } else {

@@ -38,6 +38,10 @@ constexpr int kRunLen = 8;             // maximum G run length (compile-time)
 // default real-space cutoff of the mixed path: erfc(alpha r_c) = kMixedRealTol
 // (the FP64 path and every G cutoff use 1e-16)
 constexpr double kMixedRealTol = 1e-10;
+// tiered FP64 path: pair images with erfc(alpha r) above kTierErfc are
+// evaluated in FP64, the rest in FP32
+constexpr double kTierErfc = 1e-7;
+constexpr int kHeadCap = 64;           // per-warp queue of FP64 (head) terms of the tiered path
 constexpr int kRealUnits = 16;         // work units (sub-tiles x j slices) of one pair item, at most
 
 // FP64 image vector (x, y, z, unused), 32-byte aligned for two 16-byte loads.
@@ -60,10 +64,12 @@ struct SysDev {
     float alpha_f, rc2_f, coin2_f;
     float alpha_lo_f, alpha2_f, alpha2_lo_f;  // alpha = alpha_f + alpha_lo_f, alpha^2 likewise
     float close2_f;  // FP32 path: pairs closer than this (squared) get their R = 0 term in FP64
+    float tier2_f;   // tiered FP64 path (> 0): images with r^2 below this are evaluated in FP64
     // real space
     int n_img, sub_bits, cand_max;  // images [n_img + 1]: the last is a far sentinel
     const Img64 *img_d;
     const float4 *img_f;
+    const float4 *img_lo_f;  // img_d - img_f: the rounding of the FP32 images (tiered path)
     const unsigned short *cand;
     int tile, n_mob_tiles, n_items;  // pair tiles (T = tile) and items per walker
     const int2 *items;               // (ti, tj); tj >= n_mob_tiles -> fixed tile tj - n_mob_tiles
@@ -111,6 +117,7 @@ struct BatchDev {
 // Host-side tables built in FP64 by setup.cpp.
 struct HostTables {
     int dim = 0, n_mob = 0, n_fix = 0, precision = 0, resum_every = 64;
+    bool tiered = false;  // EWALD_FP64_TIERED: precision is EWALD_FP64, real space tiered
     double A[3][3] = {}, Ainv[3][3] = {}, B[3][3] = {};  // B rows = b_k, a_i.b_j = 2 pi d_ij
     double volume = 0, alpha = 0, r_c = 0, g_c = 0;
     std::vector<double> q_mob, q_fix, fix_pos;

@@ -587,7 +587,10 @@ int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
         return EWALD_ERR_ARG;
     }
     if (d->n_mobile > (1 << 20) || d->n_fixed > (1 << 20)) { *why = "too many particles"; return EWALD_ERR_ARG; }
-    if (d->precision != EWALD_FP64 && d->precision != EWALD_MIXED) { *why = "bad precision"; return EWALD_ERR_ARG; }
+    if (d->precision != EWALD_FP64 && d->precision != EWALD_MIXED && d->precision != EWALD_FP64_TIERED) {
+        *why = "bad precision";
+        return EWALD_ERR_ARG;
+    }
     int dim = d->dim;
     if (!all_finite(d->lattice, dim * dim) || !all_finite(d->mobile_charge, d->n_mobile) ||
         (d->n_fixed && (!all_finite(d->fixed_pos, (size_t)d->n_fixed * dim) ||
@@ -605,7 +608,9 @@ int build_tables(const ewald_desc *d, HostTables *t, std::string *why) {
     t->dim = dim;
     t->n_mob = d->n_mobile;
     t->n_fix = d->n_fixed;
-    t->precision = d->precision;
+    // the tiered form is the FP64 form with a tiered real-space kernel
+    t->tiered = d->precision == EWALD_FP64_TIERED;
+    t->precision = t->tiered ? EWALD_FP64 : d->precision;
     t->resum_every = d->resum_every > 0 ? d->resum_every : 64;
     t->q_mob.assign(d->mobile_charge, d->mobile_charge + d->n_mobile);
     t->q_fix.assign(d->fixed_charge, d->fixed_charge + d->n_fixed);

@@ -15,7 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-EWALD_FP64, EWALD_MIXED = 0, 1
+EWALD_FP64, EWALD_MIXED, EWALD_FP64_TIERED = 0, 1, 2
+PRECISIONS = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED, "fp64_tiered": EWALD_FP64_TIERED}
 ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_LATTICE", 3: "ERR_COINCIDENT", 4: "ERR_NO_PROPOSAL",
              5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
 
@@ -172,7 +173,7 @@ class Context:
         nf = 0 if fixed_charge is None else len(fixed_charge)
         self._fp = _f64(fixed_pos if nf else np.zeros(1))
         self._fq = _f64(fixed_charge if nf else np.zeros(1))
-        prec = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED}.get(precision, precision)
+        prec = PRECISIONS.get(precision, precision)
         # heights of a layered 2D cell (None: every particle in the plane)
         self._zm = None if mobile_z is None else _f64(mobile_z)
         self._zf = None if fixed_z is None or nf == 0 else _f64(fixed_z)
@@ -428,7 +429,7 @@ def tune_alpha(dim, lattice, mobile_charge, pos, fixed_pos=None, fixed_charge=No
     fq = _f64(fixed_charge if nf else np.zeros(1))
     zm = None if mobile_z is None else _f64(mobile_z)
     zf = None if fixed_z is None or nf == 0 else _f64(fixed_z)
-    prec = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED}.get(precision, precision)
+    prec = PRECISIONS.get(precision, precision)
     d = Desc(int(dim), lat.ctypes.data_as(_dp), len(qm), qm.ctypes.data_as(_dp), nf, fp.ctypes.data_as(_dp),
              fq.ctypes.data_as(_dp), float(alpha), 0.0, 0.0, int(prec), 0,
              None if zm is None else zm.ctypes.data_as(_dp), None if zf is None else zf.ctypes.data_as(_dp))
