@@ -255,7 +255,7 @@ int ewald_server_create(int precision, int max_walkers, double hbm_budget_bytes,
     if (!e) e = cudaMemGetInfo(&free_b, &total_b);
     s->budget = hbm_budget_bytes > 0 ? (size_t)hbm_budget_bytes : (size_t)(0.8 * (double)free_b);
     // keep freed request memory in the stream-ordered pool instead of
-    // returning it to the driver at every synchronisation
+    // returning it to the CUDA driver at every synchronisation
     if (!e) {
         int dev = 0;
         cudaMemPool_t pool;
