@@ -714,7 +714,7 @@ int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device) {
     ewald_ctx *c = b->ctx;
     if (int r = ensure_rho(b)) return r;
     double *dst = on_device ? rho_out : b->d_io;
-    int e = launch_rho_out(c->s, b->b, c->d_g2slot, dst, c->stream);
+    int e = launch_rho_out(c->s, b->b, c->t.precision, c->d_g2slot, dst, c->stream);
     if (e) return cuda_fail(c, (cudaError_t)e);
     if (on_device) return EWALD_OK;
     return copy_out(b, rho_out, b->d_io, (size_t)b->b.W * c->s.n_layers * c->s.n_gh * 2 * sizeof(double), 0);

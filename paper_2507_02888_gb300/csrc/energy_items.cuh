@@ -57,6 +57,11 @@ struct SlotSum<float> {
         s = u;
     }
     __device__ double get() const { return (double)s - (double)c; }
+    // s - c as an unevaluated float pair hi + lo, exactly (|c| <= ulp(s))
+    __device__ void split(float &hi, float &lo) const {
+        hi = __fsub_rn(s, c);
+        lo = __fsub_rn(__fsub_rn(s, hi), c);
+    }
 };
 
 // One thread's run over the tile's electrons: the run's first G from three
@@ -196,16 +201,33 @@ __device__ __forceinline__ void sfac_item_body(const SysDev &s, const BatchDev &
                 if (r < s.run_len) {
                     const int slot = r * s.n_runs + run;
                     double2 v = make_double2(0.0, 0.0);
-                    if (r < rn.w) {
-                        v.x = ax[r].get();
-                        v.y = ay[r].get();
-                        if (rfix) {
+                    if constexpr (sizeof(R) == 4) {
+                        // the float pair of the compensated sum goes to memory as it is
+                        float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+                        if (r < rn.w) {
+                            ax[r].split(hx, lx);
+                            ay[r].split(hy, ly);
+                        }
+                        v = make_double2((double)hx + (double)lx, (double)hy + (double)ly);
+                        if (rfix && r < rn.w) {
                             v.x += rfix[slot].x;
                             v.y += rfix[slot].y;
+                            RhoIO<R>::set(rho, slot, v);
+                        } else {
+                            ((float4 *)rho)[slot] = make_float4(hx, hy, lx, ly);
                         }
-                        if (nl == 1) epart += s.gw_d[slot] * (v.x * v.x + v.y * v.y);
+                    } else {
+                        if (r < rn.w) {
+                            v.x = ax[r].get();
+                            v.y = ay[r].get();
+                            if (rfix) {
+                                v.x += rfix[slot].x;
+                                v.y += rfix[slot].y;
+                            }
+                        }
+                        RhoIO<R>::set(rho, slot, v);
                     }
-                    rho[slot] = v;
+                    if (nl == 1 && r < rn.w) epart += s.gw_d[slot] * (v.x * v.x + v.y * v.y);
                 }
             }
         }
@@ -217,10 +239,10 @@ __device__ __forceinline__ void sfac_item_body(const SysDev &s, const BatchDev &
         for (int r = 0; r < s.run_len && r < rn.w; ++r) {
             const int slot = r * s.n_runs + run;
             for (int L = 0; L < nl; ++L) {
-                const double2 a = rho[(size_t)L * slots + slot];
+                const double2 a = RhoIO<R>::get(rho, (size_t)L * slots + slot);
                 epart += s.gwl_d[((size_t)L * nl + L) * slots + slot] * (a.x * a.x + a.y * a.y);
                 for (int M = L + 1; M < nl; ++M) {
-                    const double2 c = rho[(size_t)M * slots + slot];
+                    const double2 c = RhoIO<R>::get(rho, (size_t)M * slots + slot);
                     epart += 2.0 * s.gwl_d[((size_t)L * nl + M) * slots + slot] * (a.x * c.x + a.y * c.y);
                 }
             }

@@ -112,13 +112,14 @@ __global__ void k_combine(SysDev s, BatchDev b) {
     if (w < b.W) combine_walker(s, b, w);
 }
 
+template <typename R>
 __global__ void k_rho_out(SysDev s, BatchDev b, const int *__restrict__ g2slot, double *__restrict__ out) {
     // out[W][n_layers][n_gh]: t = (w * n_layers + L) * n_gh + g
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)b.W * s.n_layers * s.n_gh) return;
     const long long wl = t / s.n_gh;
     const int g = (int)(t - wl * s.n_gh);
-    double2 v = b.rho[(size_t)wl * s.n_runs * s.run_len + g2slot[g]];
+    const double2 v = RhoIO<R>::get(b.rho, (size_t)wl * s.n_runs * s.run_len + g2slot[g]);
     out[2 * t] = v.x;
     out[2 * t + 1] = v.y;
 }
@@ -245,9 +246,11 @@ int launch_combine(const SysDev &s, const BatchDev &b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-int launch_rho_out(const SysDev &s, const BatchDev &b, const int *g2slot, double *out, cudaStream_t st) {
+int launch_rho_out(const SysDev &s, const BatchDev &b, int precision, const int *g2slot, double *out,
+                   cudaStream_t st) {
     long long n = (long long)b.W * s.n_layers * s.n_gh;
-    k_rho_out<<<(int)((n + 255) / 256), 256, 0, st>>>(s, b, g2slot, out);
+    if (precision == EWALD_FP64) k_rho_out<double><<<(int)((n + 255) / 256), 256, 0, st>>>(s, b, g2slot, out);
+    else k_rho_out<float><<<(int)((n + 255) / 256), 256, 0, st>>>(s, b, g2slot, out);
     return cudaGetLastError();
 }
 

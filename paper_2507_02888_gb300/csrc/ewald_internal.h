@@ -188,7 +188,7 @@ struct JuDev {
 
 // Kernel ids of the per-context timers (ewald_get_timing).
 enum { KT_INGEST = 0, KT_SFAC, KT_REAL, KT_COMBINE, KT_PROPOSE, KT_ACCEPT, KT_RESUM, KT_COUNT };
-int launch_rho_out(const SysDev &s, const BatchDev &b, const int *g2slot, double *out,
+int launch_rho_out(const SysDev &s, const BatchDev &b, int precision, const int *g2slot, double *out,
                    cudaStream_t st);
 
 }  // namespace ewald

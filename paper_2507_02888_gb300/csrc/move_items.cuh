@@ -134,8 +134,8 @@ __device__ __noinline__ R layered_recip_delta(const SysDev &s, const BatchDev &b
     for_each_delta<R, DIM>(s, tab, qk, [&](int slot, Cx<R> d) {
         R t = FP<R>::gwl(s, ((size_t)K * nl + K) * slots + slot) * (d.x * d.x + d.y * d.y);
         for (int L = 0; L < nl; ++L) {
-            const double2 rv = rho[(size_t)L * slots + slot];
-            t += R(2) * FP<R>::gwl(s, ((size_t)K * nl + L) * slots + slot) * ((R)rv.x * d.x + (R)rv.y * d.y);
+            const Cx<R> rv = RhoIO<R>::lead(rho, (size_t)L * slots + slot);
+            t += R(2) * FP<R>::gwl(s, ((size_t)K * nl + L) * slots + slot) * (rv.x * d.x + rv.y * d.y);
         }
         part += t;
     });
@@ -173,9 +173,8 @@ __device__ double move_delta_e(const SysDev &s, const BatchDev &b, int w, int k,
     } else {
         const double2 *rho = b.rho + (size_t)w * s.n_runs * s.run_len;
         for_each_delta<R, DIM>(s, m.tab, pold.q, [&](int slot, Cx<R> d) {
-            const double2 rv = rho[slot];
-            const R rx = (R)rv.x, ry = (R)rv.y;
-            part += FP<R>::gw(s, slot) * (R(2) * (rx * d.x + ry * d.y) + d.x * d.x + d.y * d.y);
+            const Cx<R> rv = RhoIO<R>::lead(rho, slot);
+            part += FP<R>::gw(s, slot) * (R(2) * (rv.x * d.x + rv.y * d.y) + d.x * d.x + d.y * d.y);
         });
     }
     tot += (double)part;
@@ -189,10 +188,7 @@ __device__ void move_apply_rho(const SysDev &s, const BatchDev &b, int w, int k,
     const size_t slots = (size_t)s.n_runs * s.run_len;
     double2 *rho = b.rho + ((size_t)w * s.n_layers + (DIM == 2 && s.n_layers > 1 ? s.mob_layer[k] : 0)) * slots;
     for_each_delta<R, DIM>(s, m.tab, qk, [&](int slot, Cx<R> d) {
-        double2 rv = rho[slot];
-        rv.x += (double)d.x;
-        rv.y += (double)d.y;
-        rho[slot] = rv;
+        RhoIO<R>::add(rho, slot, d);
     });
 }
 
