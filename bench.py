@@ -191,9 +191,11 @@ def move_roofline(info, w, W, moves_per_s, accept_frac, peaks, hbm_peak, hbm_bas
     if not moves_per_s:
         return None
     n, nf, dim, ngh = w["n"], len(w["fixed_q"]), w["dim"], info["n_g_half"]
-    # propose: rho(G) of the walker and every particle's position; accept:
-    # rho(G) read-modify-write and the moved position, for accepted moves
-    bytes_move = ngh * 16 + (n + nf) * dim * 8 + accept_frac * (2 * ngh * 16 + dim * 8)
+    # propose: rho(G) of the walker (the mixed path reads its FP32 leading
+    # pair, 8 bytes a G) and every particle's position; accept: rho(G)
+    # read-modify-write (16 bytes a G each way) and the moved position, for
+    # accepted moves
+    bytes_move = ngh * 8 + (n + nf) * dim * 8 + accept_frac * (2 * ngh * 16 + dim * 8)
     dim_ball = 4.0 / 3.0 * math.pi * info["r_cutoff"] ** 3 if dim == 3 else math.pi * info["r_cutoff"] ** 2
     terms = 2 * (n - 1 + nf) * dim_ball / info["volume"]      # old and new position against all others
     flop_move = terms * FLOP_REAL_TERM + 2 * ngh * FLOP_G_TERM
