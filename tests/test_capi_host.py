@@ -68,3 +68,35 @@ def test_create_rejects_bad_descriptions(case, code):
         got, h = _create(precision=7)
     assert got == code
     assert not h.value
+
+
+def _create_z(dim, n, z, zf=None, nf=0, precision=0, alpha=0.5):
+    lib = ewald.load()
+    lat = np.ascontiguousarray(np.eye(dim) * 9.0, dtype=np.float64)
+    q = np.ascontiguousarray(-np.ones(n))
+    zz = np.ascontiguousarray(z, dtype=np.float64)
+    fp = np.ascontiguousarray(np.zeros((max(nf, 1), dim)))
+    fq = np.ascontiguousarray(np.ones(max(nf, 1)))
+    zfa = None if zf is None else np.ascontiguousarray(zf, dtype=np.float64)
+    d = ewald.Desc(dim, lat.ctypes.data_as(ewald._dp), n, q.ctypes.data_as(ewald._dp), nf,
+                   fp.ctypes.data_as(ewald._dp), fq.ctypes.data_as(ewald._dp), alpha, 0.0, 0.0, precision, 0,
+                   zz.ctypes.data_as(ewald._dp), None if zfa is None else zfa.ctypes.data_as(ewald._dp))
+    h = ctypes.c_void_p()
+    return lib.ewald_create(ctypes.byref(d), None, ctypes.byref(h)), h
+
+
+@pytest.mark.parametrize("case", ["heights_in_3d", "nan_height", "five_heights", "far_layers", "nan_fixed_height"])
+def test_create_rejects_bad_heights(case):
+    # layered 2D cells (Eqs. (5)-(6) at z != 0): every check runs on the host
+    if case == "heights_in_3d":
+        got, h = _create_z(3, 4, [0.0, 1.0, 0.0, 1.0])
+    elif case == "nan_height":
+        got, h = _create_z(2, 4, [0.0, np.nan, 0.0, 1.0])
+    elif case == "five_heights":
+        got, h = _create_z(2, 5, [0.0, 1.0, 2.0, 3.0, 4.0])
+    elif case == "far_layers":
+        got, h = _create_z(2, 4, [0.0, 1e6, 0.0, 1e6])      # |dz| g_c far beyond 600
+    else:
+        got, h = _create_z(2, 4, [0.0, 1.0, 0.0, 1.0], zf=[np.nan], nf=1)
+    assert got == 1
+    assert not h.value
