@@ -57,7 +57,11 @@ __global__ void __launch_bounds__(kMoveThreads)
         set_lo<R>(pnew, d, su_new[d]);
     }
     pold.q = pnew.q = FP<R>::q_mob(s, k);
-    pold.z = pnew.z = DIM == 2 && s.n_layers > 1 ? FP<R>::z_mob(s, k) : R(0);
+    if (DIM == 2) {  // after the coordinates: the FP64 height shares the third word
+        const R z = s.n_layers > 1 ? FP<R>::z_mob(s, k) : R(0);
+        set_part_z(pold, z);
+        set_part_z(pnew, z);
+    }
     build_move_tables<R, DIM>(s, pold.u, pnew.u, m.tab);
     __syncthreads();
 

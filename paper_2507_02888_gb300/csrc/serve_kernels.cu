@@ -117,7 +117,11 @@ __global__ void __launch_bounds__(kMoveThreads, kServeMinBlocks) k_serve_step(Se
             set_lo<R>(pnew, q, s_unew[q]);
         }
         pold.q = pnew.q = FP<R>::q_mob(ss, k);
-        pold.z = pnew.z = dim == 2 && ss.n_layers > 1 ? FP<R>::z_mob(ss, k) : R(0);
+        if (dim == 2) {  // after the coordinates: the FP64 height shares the third word
+            const R z = ss.n_layers > 1 ? FP<R>::z_mob(ss, k) : R(0);
+            set_part_z(pold, z);
+            set_part_z(pnew, z);
+        }
         if (dim == 3) build_move_tables<R, 3>(ss, pold.u, pnew.u, m.tab);
         else build_move_tables<R, 2>(ss, pold.u, pnew.u, m.tab);
         __syncthreads();
