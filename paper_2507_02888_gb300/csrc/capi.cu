@@ -11,6 +11,8 @@
 #include <sstream>
 #include <new>
 #include <utility>
+
+#include "sfac_df.h"
 #include <string>
 #include <vector>
 
@@ -203,6 +205,13 @@ int build_device(ewald_ctx *c) {
     return apply_tiling(c, S, t.sub_bits);
 }
 
+// The structure factor of a context's batch: the tiered FP64 form takes the
+// double-float kernel, every other form its own precision's.
+int run_sfac(ewald_ctx *c, const BatchDev &b, int precision, const unsigned char *only) {
+    if (c->t.tiered) return launch_sfac_df(c->s, b, c->cfg, only, c->stream);
+    return launch_sfac(c->s, b, precision, c->cfg, only, c->stream);
+}
+
 cudaEvent_t take_event(ewald_ctx *c) {
     if (!c->ev_pool.empty()) {
         cudaEvent_t e = c->ev_pool.back();
@@ -319,7 +328,7 @@ const void *copy_in(ewald_batch *b, const void *src, size_t n, void *dscratch, i
 int run_energy(ewald_batch *b) {
     ewald_ctx *c = b->ctx;
     const int p = c->t.precision;
-    int e = timed(c, KT_SFAC, [&] { return launch_sfac(c->s, b->b, p, c->cfg, nullptr, c->stream); });
+    int e = timed(c, KT_SFAC, [&] { return run_sfac(c, b->b, p, nullptr); });
     if (!e) e = timed(c, KT_REAL, [&] { return launch_real(c->s, b->b, p, c->cfg, c->stream); });
     if (!e) e = timed(c, KT_COMBINE, [&] { return launch_combine(c->s, b->b, c->stream); });
     if (e) return cuda_fail(c, (cudaError_t)e);
@@ -332,7 +341,7 @@ int run_energy(ewald_batch *b) {
 int ensure_rho(ewald_batch *b) {
     if (!b->rho_stale) return EWALD_OK;
     ewald_ctx *c = b->ctx;
-    int e = timed(c, KT_RESUM, [&] { return launch_sfac(c->s, b->b, c->t.precision, c->cfg, nullptr, c->stream); });
+    int e = timed(c, KT_RESUM, [&] { return run_sfac(c, b->b, c->t.precision, nullptr); });
     if (e) return cuda_fail(c, (cudaError_t)e);
     b->rho_stale = false;
     return EWALD_OK;
@@ -696,7 +705,7 @@ int ewald_accept_move(ewald_batch *b, const unsigned char *accept, int on_device
     const int p = c->t.precision;
     int e = timed(c, KT_ACCEPT, [&] { return launch_accept(c->s, b->b, p, c->cfg, da, c->t.resum_every, c->stream); });
     // rebuild rho(G) of the walkers that reached resum_every accepted moves
-    if (!e) e = timed(c, KT_RESUM, [&] { return launch_sfac(c->s, b->b, p, c->cfg, b->b.resum_flag, c->stream); });
+    if (!e) e = timed(c, KT_RESUM, [&] { return run_sfac(c, b->b, p, b->b.resum_flag); });
     if (e) return cuda_fail(c, (cudaError_t)e);
     b->has_pending = false;
     if (!on_device) return sync_status(b);

@@ -215,3 +215,63 @@ def test_argument_checks(ew):
         ew.context_for(w, mobile_z=zz)
     with pytest.raises(ew.EwaldError):
         ew.context_for(w, mobile_z=w["z"] * 1e5)                    # |dz| g_c beyond 600
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_served_layered_moves_match_oracle(ew, prec):
+    """The serving kernel's device-drawn moves on a bilayer, replayed on the
+    host (SplitMix64 + Box-Muller, as in the in-plane serving test) with the
+    oracle's pair-definition dE."""
+    import math
+    from paper_2507_02888_gb300 import serve
+    mask = (1 << 64) - 1
+
+    def splitmix_out(seed, c):
+        z = (seed + 0x9E3779B97F4A7C15 * (c + 1)) & mask
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        return z ^ (z >> 31)
+
+    def u53(x):
+        return (x >> 11) * 2.0 ** -53
+
+    w = bilayer(n=40, W=3, sep=1.7, seed=31)
+    sigma, steps, seed, accept_p = 0.9, 10, 777, 0.5
+    ctx = ew.context_for(w, precision=prec)
+    info = ctx.info()
+    rc, gc = info["r_cutoff"], info["g_cutoff"]
+    srv = serve.Server(prec, max_walkers=8)
+    rid = srv.submit(ctx, w["pos"], steps, sigma, accept_p, seed)
+    res = None
+    for _ in range(200):
+        srv.step()
+        res = srv.result(rid)
+        if res is not None:
+            break
+    e_gpu, n_gpu, _ = res
+    lat = np.asarray(w["lattice"])
+    inv = np.linalg.inv(lat)
+    n = w["n"]
+    for walker in range(3):
+        frac = (w["pos"][walker] @ inv) % 1.0
+        e0, c0 = oracle.energy_z(lat, frac @ lat, w["z"], w["q"], w["alpha"], rc, gc)
+        floor = max(abs(e0), 1e-2 * scale(c0))
+        e, n_acc = e0, 0
+        for step in range(steps):
+            c = ((step << 32) + walker) * 8
+            k = ((splitmix_out(seed, c) >> 32) * n) >> 32
+            g = []
+            for p in range(2):
+                u1, u2 = u53(splitmix_out(seed, c + 1 + 2 * p)), u53(splitmix_out(seed, c + 2 + 2 * p))
+                rad = math.sqrt(-2.0 * math.log(1.0 - u1))
+                g += [rad * math.cos(2 * math.pi * u2), rad * math.sin(2 * math.pi * u2)]
+            acc = u53(splitmix_out(seed, c + 5)) < accept_p
+            pos = frac @ lat
+            r_new = pos[k] + sigma * np.array(g[:2])
+            de = oracle.delta_e_z(lat, pos, w["z"], w["q"], k, r_new, w["alpha"], rc, gc)
+            if acc:
+                e += de
+                n_acc += 1
+                frac[k] = (r_new @ inv) % 1.0
+        assert n_gpu[walker] == n_acc
+        assert abs(e_gpu[walker] - e) <= 2 * TOL[prec] * floor, (walker, e_gpu[walker], e)
