@@ -267,7 +267,7 @@ int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *re
  * the system and the GPU.  For desc (r_cutoff and g_cutoff must be <= 0:
  * they follow alpha) this times the full energy of the sample pos
  * [n_walkers][N][dim] (host memory, Cartesian) on trial contexts at alpha =
- * a0 x {0.6 ... 2} around a0 (desc->gamma if > 0, else the balanced
+ * a0 x {0.6 ... 3} around a0 (desc->gamma if > 0, else the balanced
  * default), refines around the fastest, and returns it in *alpha_out and
  * its time per walker (microseconds) in *us_per_walker (may be NULL).
  * Trials the cell cannot take (cutoffs too large) are skipped.  Uses

@@ -65,7 +65,7 @@ extern "C" int ewald_tune_alpha(const ewald_desc *desc, void *cuda_stream, int n
         cudaFree(e_dev);
         return EWALD_ERR_CUDA;
     }
-    const double grid[] = {0.6, 0.75, 0.9, 1.15, 1.3, 1.5, 1.75, 2.0};
+    const double grid[] = {0.6, 0.75, 0.9, 1.15, 1.3, 1.5, 1.75, 2.0, 2.4, 3.0};
     for (double m : grid) {
         const double t = time_alpha(*desc, a0 * m, cuda_stream, n_walkers, pos, e_dev);
         if (t >= 0 && t < best_t) best_t = t, best_a = a0 * m;

@@ -29,7 +29,7 @@ def scale(c):
 def test_tuned_alpha_gives_the_same_energy(ew, name, prec, tol):
     w = I.workload(name, 8)
     a, us = ew.tune_alpha(w["dim"], w["lattice"], w["q"], w["pos"], alpha=w["alpha"], precision=prec)
-    assert 0.6 * 0.93 * w["alpha"] * (1 - 1e-12) <= a <= 2.0 * 1.07 * w["alpha"] * (1 + 1e-12)
+    assert 0.6 * 0.93 * w["alpha"] * (1 - 1e-12) <= a <= 3.0 * 1.07 * w["alpha"] * (1 + 1e-12)
     assert us > 0
     ctx = ew.context_for(w, precision=prec, alpha=a)
     info = ctx.info()
