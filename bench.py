@@ -162,7 +162,7 @@ def source_hash(files):
 
 REAL_SOURCES = ["paper_2507_02888_gb300/csrc/energy_kernels.cu", "paper_2507_02888_gb300/csrc/energy_items.cuh",
                 "paper_2507_02888_gb300/csrc/ewald_internal.h",
-                "paper_2507_02888_gb300/csrc/device_common.cuh"]
+                "paper_2507_02888_gb300/csrc/device_common.cuh", "paper_2507_02888_gb300/csrc/df_math.cuh"]
 
 
 def profiled_traffic(workload, precision):

@@ -159,6 +159,19 @@ int build_device(ewald_ctx *c) {
     if ((e = upload(o, (float **)&s.q_mob_f, qmf.data(), qmf.size()))) return cuda_fail(c, e);
     if ((e = upload(o, (double **)&s.q_fix, t.q_fix.data(), t.q_fix.size()))) return cuda_fail(c, e);
     if ((e = upload(o, (float **)&s.q_fix_f, qff.data(), qff.size()))) return cuda_fail(c, e);
+    {
+        auto pairs = [](const std::vector<double> &q) {
+            std::vector<float2> v(std::max<size_t>(q.size(), 1), make_float2(0.f, 0.f));
+            for (size_t i = 0; i < q.size(); ++i) {
+                const float h = (float)q[i];
+                v[i] = make_float2(h, (float)(q[i] - (double)h));
+            }
+            return v;
+        };
+        const std::vector<float2> qm = pairs(t.q_mob), qf = pairs(t.q_fix);
+        if ((e = upload(o, (float2 **)&s.q_mob_df, qm.data(), qm.size()))) return cuda_fail(c, e);
+        if ((e = upload(o, (float2 **)&s.q_fix_df, qf.data(), qf.size()))) return cuda_fail(c, e);
+    }
     std::vector<unsigned long long> fu((size_t)dim * s.fix_stride, 0ull);
     for (int I = 0; I < t.n_fix; ++I)
         for (int k = 0; k < dim; ++k) {

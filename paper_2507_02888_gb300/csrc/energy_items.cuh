@@ -338,15 +338,18 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
         CloseList cl{cbase + warp * kCloseCap, 0};
         if constexpr (TIER) {
             HeadQueue hq{hbase + warp * kHeadCap, 0};
+            DF hacc = {0.0f, 0.0f};  // head terms, double-float
             for (int jj = j_lo; jj < j_lo + jlen; ++jj) {
                 const int lj = c * 32 + jj;
-                pair_images_tiered<DIM>(s, pi, tj[lj], valid(jj), ims.img, img_lo, ims.cand, wq, hq, acc, lane,
-                                        ((unsigned)li << 16) | (unsigned)lj, ti, tj, i0, j0, fixedj);
+                pair_images_tiered<DIM>(s, pi, tj[lj], valid(jj), ims.img, img_lo, ims.cand, wq, hq, acc, hacc,
+                                        lane, ((unsigned)li << 16) | (unsigned)lj, ti, tj, i0, j0, fixedj);
             }
             wq.drain(acc, tk, lane);
             __syncwarp();
-            if (lane < hq.n) acc.add64(head_term<DIM>(s, ti, tj, i0, j0, fixedj, hq.q[lane], b.status));
+            if (lane < hq.n)
+                head_term_df<DIM>(s, ti, tj, ims.img, img_lo, i0, j0, fixedj, hq.q[lane], b.status, hacc);
             __syncwarp();
+            acc.add64(df_to(hacc));
         } else {
             for (int jj = j_lo; jj < j_lo + jlen; ++jj) {
                 const int lj = c * 32 + jj;

@@ -84,6 +84,7 @@ struct SysDev {
     // charges and fixed particles
     const double *q_mob, *q_fix;
     const float *q_mob_f, *q_fix_f;
+    const float2 *q_mob_df, *q_fix_df;  // charges as float pairs hi + lo (tiered path)
     const unsigned long long *fix_u;  // [dim][fix_stride]
     // constants (FP64)
     double e_madR, e_self, e_bg, e_II;

@@ -19,63 +19,11 @@
 // carries ~1e-13 of relative error, inside the FP64 form's 1e-12 bound.
 #include <algorithm>
 
+#include "df_math.cuh"
 #include "energy_items.cuh"
 #include "sfac_df.h"
 
 namespace ewald {
-
-struct DF {
-    float h, l;
-};
-struct CDF {
-    DF x, y;
-};
-
-__device__ __forceinline__ DF df_from(double v) {
-    const float h = __double2float_rn(v);
-    return {h, __double2float_rn(v - (double)h)};
-}
-__device__ __forceinline__ double df_to(DF a) { return (double)a.h + (double)a.l; }
-
-// a + b
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    const float s = __fadd_rn(a.h, b.h), bp = __fsub_rn(s, a.h);
-    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bp)), __fsub_rn(b.h, bp));
-    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
-    const float h = __fadd_rn(s, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, s))};
-}
-
-// a * b + sg * c * d (sg = +-1): the two leading products exactly (FMA
-// residuals), their sum by two-sum, the cross terms into the residual
-__device__ __forceinline__ DF df_dot2(DF a, DF b, DF c, DF d, float sg) {
-    const float p1 = __fmul_rn(a.h, b.h), e1 = __fmaf_rn(a.h, b.h, -p1);
-    const float cs = sg * c.h;
-    const float p2 = __fmul_rn(cs, d.h), e2 = __fmaf_rn(cs, d.h, -p2);
-    const float s = __fadd_rn(p1, p2), bp = __fsub_rn(s, p1);
-    float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bp)), __fsub_rn(p2, bp));
-    t = __fadd_rn(t, __fadd_rn(e1, e2));
-    t = __fmaf_rn(a.h, b.l, t);
-    t = __fmaf_rn(a.l, b.h, t);
-    t = __fmaf_rn(cs, d.l, t);
-    t = __fmaf_rn(sg * c.l, d.h, t);
-    const float h = __fadd_rn(s, t);
-    return {h, __fsub_rn(t, __fsub_rn(h, s))};
-}
-
-__device__ __forceinline__ CDF cdf_mul(const CDF &a, const CDF &b) {
-    return {df_dot2(a.x, b.x, a.y, b.y, -1.0f), df_dot2(a.x, b.y, a.y, b.x, 1.0f)};
-}
-
-// a * q for a double-float q
-__device__ __forceinline__ DF df_mul(DF a, DF q) {
-    const float p = __fmul_rn(a.h, q.h);
-    float e = __fmaf_rn(a.h, q.h, -p);
-    e = __fmaf_rn(a.h, q.l, e);
-    e = __fmaf_rn(a.l, q.h, e);
-    const float h = __fadd_rn(p, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, p))};
-}
 
 struct SfacTileDF {
     const Part<double> *tp;
