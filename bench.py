@@ -377,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
         f_e, f_m, f_t, _ = timed_steps(b, ctx, fs, 1, M)
         f_e, f_m = max_over_ranks([f_e, f_m])
         e_fp64 = e_d.cpu().numpy().copy()
+        de_fp64 = de_d.cpu().numpy().copy()
         comp = b.components()
         floor = np.maximum(np.abs(comp.sum(axis=1)),
                            1e-2 * (np.abs(comp[:, 0]) + np.abs(comp[:, 2]) + np.abs(comp[:, 1] + comp[:, 3])
@@ -407,8 +408,11 @@ def run_ours(args, rank, world, local_rank):
         g_e, g_m, g_t, _ = timed_steps(b, ctx, fs, 1, M)
         g_e, g_m = max_over_ranks([g_e, g_m])
         rel_g = (e_d.cpu().numpy() - e_fp64) / floor
+        rel_de = (de_d.cpu().numpy() - de_fp64) / floor[None, :] if M else np.zeros(1)
         result["fp64_tiered"] = {"value": world * W * fs / (g_e / 1e3), "unit": "walker energies/s",
-                                 "steps": fs, "vs_fp64_max": float(np.max(np.abs(rel_g))), "gate": 1e-12,
+                                 "moves": world * W * M * fs / (g_m / 1e3) if M else None,
+                                 "steps": fs, "vs_fp64_max": float(np.max(np.abs(rel_g))),
+                                 "move_de_vs_fp64_max": float(np.max(np.abs(rel_de))), "gate": 1e-12,
                                  "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 3)
                                                           for k, v in g_t.items() if v[1]}}
         b.close()

@@ -10,14 +10,14 @@
 #include <map>
 #include <sstream>
 #include <new>
-#include <utility>
-
-#include "sfac_df.h"
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "capi_internal.h"
+#include "move_tiered.h"
 #include "multi.h"
+#include "sfac_df.h"
 
 using namespace ewald;
 
@@ -698,7 +698,10 @@ int ewald_propose_move(ewald_batch *b, const int *k, const double *r_new, double
     }
     double *dde = on_device ? de_out : b->d_de;
     if (int r = ensure_rho(b)) return r;
-    int e = timed(c, KT_PROPOSE, [&] { return launch_propose(c->s, b->b, c->t.precision, c->cfg, dk, dr, dde, c->stream); });
+    int e = timed(c, KT_PROPOSE, [&] {
+        if (c->t.tiered) return launch_propose_tiered(c->s, b->b, dk, dr, dde, c->stream);
+        return launch_propose(c->s, b->b, c->t.precision, c->cfg, dk, dr, dde, c->stream);
+    });
     if (e) return cuda_fail(c, (cudaError_t)e);
     b->has_pending = true;
     if (on_device) return EWALD_OK;

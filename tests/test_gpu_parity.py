@@ -16,7 +16,7 @@ from paper_2507_02888_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-6}
+TOL = {"fp64": 1e-12, "mixed": 1e-6, "fp64_tiered": 1e-12}
 MIXED_REAL_TOL = 1e-10   # default real-space cutoff tolerance of the mixed path
 
 
@@ -157,7 +157,7 @@ def test_rho_matches_oracle(ew, prec):
     assert all(tuple(-v) not in keys for v in nv) and (0, 0, 0) not in keys
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
 @pytest.mark.parametrize("case", ["sc54", "hex70", "diamond1"])
 def test_move_sequence_matches_oracle(ew, case, prec):
     W = 5
@@ -192,7 +192,7 @@ def test_move_sequence_matches_oracle(ew, case, prec):
     assert np.max(np.abs(frac - np.round(frac))) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
 def test_rho_after_many_moves_without_resum(ew, prec):
     """rho(G) updated in FP64 by accepted moves stays close to a rebuild."""
     W = 4
@@ -207,7 +207,7 @@ def test_rho_after_many_moves_without_resum(ew, prec):
     r1 = b.rho()
     b.resum()
     r2 = b.rho()
-    tol = 1e-12 if prec == "fp64" else 2e-5
+    tol = 2e-5 if prec == "mixed" else 1e-12
     assert np.max(np.abs(r1 - r2)) < tol * np.sqrt(w["n"])
 
 

@@ -135,3 +135,68 @@ def test_tiered_layered_bilayer(ew):
     for k in range(2):
         eo, co = oracle.energy_z(lat, w["pos"][k], w["z"], w["q"], w["alpha"], info["r_cutoff"], info["g_cutoff"])
         assert abs(e[k] - eo) <= TOL * max(abs(eo), 1e-2 * scale(co))
+
+
+def all_of(w, k, pos):
+    return np.concatenate([pos, w["fixed_pos"]]), np.concatenate([w["q"], w["fixed_q"]])
+
+
+@pytest.mark.parametrize("name", ["fcc100_odd_q", "clustered", "diamond1"])
+def test_tiered_moves_match_oracle(ew, name):
+    """Proposed dE of the tiered kernel (real space split like the energy's,
+    reciprocal in FP64) against the oracle's, through accepted and rejected
+    moves, and the energy at the end against a fresh oracle energy."""
+    W = 3
+    w = small(name, W)
+    ctx = ew.context_for(w, precision="fp64_tiered", resum_every=4)
+    info = ctx.info()
+    rc, gc = info["r_cutoff"], info["g_cutoff"]
+    b = ew.Batch(ctx, W)
+    b.set_positions(w["pos"])
+    pos = w["pos"].copy()
+    floors = []
+    for k in range(W):
+        eo, co = oracle.energy(w["dim"], w["lattice"], *all_of(w, k, pos[k]), w["alpha"], rc, gc)
+        floors.append(max(abs(eo), 1e-2 * scale(co)))
+    rng = np.random.default_rng(31)
+    ks, disp, acc = I.move_stream(rng, W, w["n"], 10, w["dim"], 0.3)
+    for m in range(ks.shape[0]):
+        rn = pos[np.arange(W), ks[m]] + disp[m]
+        de = b.propose(ks[m], rn).copy()
+        for k in range(W):
+            deo = oracle.delta_e(w["dim"], w["lattice"], *all_of(w, k, pos[k]), int(ks[m, k]), rn[k], w["alpha"],
+                                 rc, gc)
+            assert abs(de[k] - deo) <= TOL * floors[k], (m, k, de[k], deo)
+        b.accept(acc[m])
+        for k in range(W):
+            if acc[m, k]:
+                pos[k, ks[m, k]] = rn[k]
+    e = b.energy()
+    for k in range(W):
+        eo, co = oracle.energy(w["dim"], w["lattice"], *all_of(w, k, pos[k]), w["alpha"], rc, gc)
+        assert abs(e[k] - eo) <= TOL * max(abs(eo), 1e-2 * scale(co))
+
+
+def test_tiered_moves_full_size(ew):
+    """The fcc workload's 4096 walkers: every proposed dE equal to the FP64
+    kernel's within the FP64 bar, and two sampled walkers against the oracle."""
+    w = I.workload("heg3d_fcc_n1024")
+    W = w["n_walkers"]
+    rng = np.random.default_rng(8)
+    ks = rng.integers(0, w["n"], size=W)
+    rn = w["pos"][np.arange(W), ks] + rng.normal(scale=0.4, size=(W, 3))
+    out = {}
+    for prec in ("fp64", "fp64_tiered"):
+        ctx = ew.context_for(w, precision=prec)
+        b = ew.Batch(ctx, W)
+        b.set_positions(w["pos"])
+        e = b.energy().copy()
+        c = b.components().copy()
+        out[prec] = b.propose(ks, rn).copy()
+    floor = np.maximum(np.abs(e), 1e-2 * (np.abs(c[:, 0]) + np.abs(c[:, 2]) + np.abs(c[:, 1] + c[:, 3])
+                                          + np.abs(c[:, 4])))
+    assert np.max(np.abs(out["fp64_tiered"] - out["fp64"]) / floor) <= TOL
+    rc, gc = oracle.cutoffs(3, w["alpha"])
+    for k in (5, 4090):
+        deo = oracle.delta_e(3, w["lattice"], *all_of(w, k, w["pos"][k]), int(ks[k]), rn[k], w["alpha"], rc, gc)
+        assert abs(out["fp64_tiered"][k] - deo) <= TOL * floor[k], (k, out["fp64_tiered"][k], deo)
