@@ -60,6 +60,7 @@ def parse():
     p.add_argument("--no-tune-alpha", action="store_true", help="skip the measured alpha balancing leg")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-requests-fp64", type=int, default=120)
+    p.add_argument("--serve-requests-tiered", type=int, default=600)
     return p.parse_args()
 
 
@@ -500,6 +501,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_serving:
         sv = run_serving(stream, "mixed", args.serve_requests)
         sv["fp64"] = run_serving(stream, "fp64", args.serve_requests_fp64)
+        sv["fp64_tiered"] = run_serving(stream, "fp64_tiered", args.serve_requests_tiered)
         result["serving"] = sv
 
     # ---- CPU oracle on the host cores (rank 0 only)

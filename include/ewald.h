@@ -204,11 +204,14 @@ void ewald_multi_destroy(ewald_multi *m);
 
 /* Serving form: continuous batching of walker batches from concurrent runs.
  * A request is W walkers of one system (a context of the server's
- * precision) that each make n_steps single-particle moves: particle k
+ * precision, see below) that each make n_steps single-particle moves: particle k
  * uniform, Gaussian displacement of standard deviation sigma per axis,
  * accepted with probability accept_prob (there is no wave function here),
  * all drawn on the device from a counter-based SplitMix64 stream of the
- * request's seed.  Requests queue on submission and are admitted between
+ * request's seed.  precision: EWALD_MIXED takes mixed contexts, EWALD_FP64
+ * FP64 and tiered ones (moves by the plain FP64 kernel), EWALD_FP64_TIERED
+ * tiered ones (moves by the tiered kernel: real space split by term size,
+ * reciprocal part and rho(G) in FP64).  Requests queue on submission and are admitted between
  * steps while the server's walker slots and device-memory budget allow;
  * from admission on their rho(G) stays on the device.  Every step advances
  * every active request by one move in one persistent launch (replayed from

@@ -22,9 +22,10 @@ __host__ __device__ inline size_t sfac_bytes(const SysDev &s, int precision, int
 
 // tiered: the FP32 tiles and queues of the mixed path plus the head queues
 __host__ __device__ inline size_t real_work_bytes(const SysDev &s, int precision, int warps, bool tiered = false) {
-    size_t part = precision == EWALD_FP64 && !tiered ? sizeof(Part<double>) : sizeof(Part<float>);
-    size_t qe = precision == EWALD_FP64 && !tiered ? sizeof(QE<double>) : sizeof(QE<float>);
-    return 2 * align16(s.tile * part) + align16((size_t)warps * kQueueCap * qe) +
+    const bool f64 = precision == EWALD_FP64 && !tiered;
+    size_t part = f64 ? sizeof(Part<double>) : sizeof(Part<float>);
+    size_t qe = f64 ? kQueueCap64 * sizeof(QE<double>) : kQueueCap32 * sizeof(QE<float>);
+    return 2 * align16(s.tile * part) + align16((size_t)warps * qe) +
            align16((size_t)warps * kCloseCap * sizeof(unsigned)) + align16(kRealUnits * sizeof(double)) +
            (tiered ? align16((size_t)warps * kHeadCap * sizeof(uint2)) : 0);
 }
@@ -291,7 +292,7 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
     Part<R> *tj = (Part<R> *)(work + off);
     off += align16(s.tile * sizeof(Part<R>));
     QE<R> *qbase = (QE<R> *)(work + off);
-    off += align16((size_t)nw * kQueueCap * sizeof(QE<R>));
+    off += align16((size_t)nw * kQueueCapOf<R> * sizeof(QE<R>));
     unsigned *cbase = (unsigned *)(work + off);
     off += align16((size_t)nw * kCloseCap * sizeof(unsigned));
     double *red = (double *)(work + off);
@@ -310,7 +311,7 @@ __device__ void real_item(const SysDev &s, const BatchDev &b, int w, int p, cons
         tj[t] = fixedj ? load_fixed<R>(s, j0 + t, DIM) : load_mobile<R>(s, b, w, j0 + t, DIM);
     }
     __syncthreads();
-    WarpQueue<R> wq{qbase + warp * kQueueCap, 0, FP<R>::coin2(s), b.status};
+    WarpQueue<R> wq{qbase + warp * kQueueCapOf<R>, 0, FP<R>::coin2(s), b.status};
     const typename FP<R>::K tk = FP<R>::term_consts(s);
     const bool diag = !fixedj && tt.x == tt.y;
     const int nst = diag ? S * (S + 1) / 2 : S * S;

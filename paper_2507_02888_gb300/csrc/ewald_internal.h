@@ -28,8 +28,12 @@ namespace ewald {
 constexpr int kRealWarps = 4;          // warps per real-space CTA
 constexpr int kRealThreads = 32 * kRealWarps;
 // resident real-space CTAs per SM the registers are sized for (FP32, FP64 path)
-constexpr int kRealMinBlocks32 = 10, kRealMinBlocks64 = 8;
-constexpr int kQueueCap = 96;          // per-warp queue of accepted (r^2, weight) terms
+constexpr int kRealMinBlocks32 = 11, kRealMinBlocks64 = 8;
+// per-warp queues of accepted (r^2, weight) terms: the FP32 one a ring
+// flushed 64 entries at a time, the FP64 one flushed 32 at a time
+constexpr int kQueueCap32 = 128, kQueueCap64 = 96;
+template <typename R>
+constexpr int kQueueCapOf = sizeof(R) == 4 ? kQueueCap32 : kQueueCap64;
 constexpr int kSfacThreads = 256;      // threads (= runs) per structure-factor CTA, at most
 // resident structure-factor CTAs per SM the registers are sized for (FP32, FP64 path)
 constexpr int kSfacMinBlocks32 = 3, kSfacMinBlocks64 = 2;

@@ -76,7 +76,7 @@ struct MoveSmem {
         return align16(2 * per * sizeof(Cx<R>));
     }
     __host__ __device__ static size_t bytes(const SysDev &s) {
-        return ImageSmem<R>::bytes(s, s.dim) + align16((kMoveThreads / 32) * kQueueCap * sizeof(QE<R>)) +
+        return ImageSmem<R>::bytes(s, s.dim) + align16((kMoveThreads / 32) * kQueueCapOf<R> * sizeof(QE<R>)) +
                table_bytes(s) + align16((kMoveThreads / 32) * sizeof(double));
     }
     __device__ void carve(unsigned char *base, const SysDev &s, int dim) {
@@ -89,7 +89,7 @@ struct MoveSmem {
         unsigned char *base = work;
         size_t off = 0;
         queues = (QE<R> *)(base + off);
-        off += align16((kMoveThreads / 32) * kQueueCap * sizeof(QE<R>));
+        off += align16((kMoveThreads / 32) * kQueueCapOf<R> * sizeof(QE<R>));
         Cx<R> *p = (Cx<R> *)(base + off);
         const int W[3] = {2 * s.n1max + 1, 2 * s.n2max + 1, dim == 3 ? s.n3max + 1 : 0};
         for (int which = 0; which < 2; ++which)
@@ -148,7 +148,7 @@ template <typename R, int DIM>
 __device__ double move_delta_e(const SysDev &s, const BatchDev &b, int w, int k, const Part<R> &pold,
                                const Part<R> &pnew, MoveSmem<R> &m) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    WarpQueue<R> wq{m.queues + warp * kQueueCap, 0, FP<R>::coin2(s), b.status};
+    WarpQueue<R> wq{m.queues + warp * kQueueCapOf<R>, 0, FP<R>::coin2(s), b.status};
     Acc<R> acc;
     // real space: slots (other particle j, old/new), j over mobile != k then fixed
     const int n_other = s.n_mob - 1 + s.n_fix;
@@ -181,13 +181,13 @@ __device__ double move_delta_e(const SysDev &s, const BatchDev &b, int w, int k,
     return block_sum(tot, m.red);
 }
 
-// rho(G) += delta(G) of walker w's particle k (tables of m built): the
-// FP64 running sum (of k's layer in a layered cell).
+// rho(G) += delta(G) of walker w's particle k (tables built): the FP64
+// running sum (of k's layer in a layered cell).
 template <typename R, int DIM>
-__device__ void move_apply_rho(const SysDev &s, const BatchDev &b, int w, int k, R qk, MoveSmem<R> &m) {
+__device__ void move_apply_rho(const SysDev &s, const BatchDev &b, int w, int k, R qk, const MoveTables<R> &tab) {
     const size_t slots = (size_t)s.n_runs * s.run_len;
     double2 *rho = b.rho + ((size_t)w * s.n_layers + (DIM == 2 && s.n_layers > 1 ? s.mob_layer[k] : 0)) * slots;
-    for_each_delta<R, DIM>(s, m.tab, qk, [&](int slot, Cx<R> d) {
+    for_each_delta<R, DIM>(s, tab, qk, [&](int slot, Cx<R> d) {
         RhoIO<R>::add(rho, slot, d);
     });
 }

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kMoveThreads)
     pold.q = FP<R>::q_mob(s, k);
     build_move_tables<R, DIM>(s, pold.u, pnew.u, m.tab);
     __syncthreads();
-    move_apply_rho<R, DIM>(s, b, w, k, pold.q, m);
+    move_apply_rho<R, DIM>(s, b, w, k, pold.q, m.tab);
     __syncthreads();
     if (tid < DIM) b.u[((size_t)w * DIM + tid) * s.mob_stride + k] = b.pend_u[(size_t)w * 3 + tid];
     if (tid == 0) {

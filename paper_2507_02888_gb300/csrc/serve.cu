@@ -23,6 +23,7 @@
 
 #include "capi_internal.h"
 #include "serve.h"
+#include "sfac_df.h"
 
 using namespace ewald;
 using namespace ewald_capi;
@@ -221,8 +222,13 @@ int admit(ewald_server *s, Req &r) {
     if (!e) e = cudaMemcpyAsync(d_pos, r.pos.data(), r.pos.size() * sizeof(double), cudaMemcpyHostToDevice, st);
     if (!e) e = cudaMemsetAsync(b.status, 0, sizeof(int), st);
     if (!e) e = (cudaError_t)launch_ingest(sd, b, d_pos, st);
-    if (!e) e = (cudaError_t)launch_sfac(sd, b, s->precision, c->cfg, nullptr, st);
-    if (!e) e = (cudaError_t)launch_real(sd, b, s->precision, c->cfg, st);
+    if (s->precision == EWALD_FP64_TIERED) {
+        if (!e) e = (cudaError_t)launch_sfac_df(sd, b, c->cfg, nullptr, st);
+    } else {
+        if (!e) e = (cudaError_t)launch_sfac(sd, b, s->precision, c->cfg, nullptr, st);
+    }
+    // the real-space launch follows the context (tiered if it is)
+    if (!e) e = (cudaError_t)launch_real(sd, b, c->t.precision, c->cfg, st);
     if (!e) e = (cudaError_t)launch_combine(sd, b, st);  // e = E0, acc_count = 0
     if (d_pos) cudaFreeAsync(d_pos, st);
     if (!e) e = cudaMemsetAsync(s->d_n_acc + r.acc_base, 0, sizeof(int) * r.W, st);
@@ -239,7 +245,8 @@ extern "C" {
 int ewald_server_create(int precision, int max_walkers, double hbm_budget_bytes, void *stream, ewald_server **out) {
     if (!out) return EWALD_ERR_ARG;
     *out = nullptr;
-    if ((precision != EWALD_FP64 && precision != EWALD_MIXED) || max_walkers < 1) return EWALD_ERR_ARG;
+    if ((precision != EWALD_FP64 && precision != EWALD_MIXED && precision != EWALD_FP64_TIERED) || max_walkers < 1)
+        return EWALD_ERR_ARG;
     ewald_server *s = new (std::nothrow) ewald_server();
     if (!s) return EWALD_ERR_OOM;
     s->precision = precision;
@@ -322,7 +329,9 @@ int ewald_server_submit(ewald_server *s, ewald_ctx *system, const double *pos, i
     if (!s || !system || !pos || !request_id || n_walkers < 1 || n_steps < 0 || !(sigma >= 0) ||
         !(accept_prob >= 0 && accept_prob <= 1))
         return srv_fail(s, EWALD_ERR_ARG, "bad request");
-    if (system->t.precision != s->precision) return srv_fail(s, EWALD_ERR_ARG, "system precision differs from the server's");
+    // an FP64 server takes FP64 and tiered contexts, a tiered server tiered ones
+    const bool ok = s->precision == EWALD_FP64_TIERED ? system->t.tiered : system->t.precision == s->precision;
+    if (!ok) return srv_fail(s, EWALD_ERR_ARG, "system precision differs from the server's");
     if (n_walkers > s->max_walkers) return srv_fail(s, EWALD_ERR_ARG, "more walkers than the server's slots");
     const size_t nb = request_bytes(system, n_walkers);
     if (nb > s->budget) return srv_fail(s, EWALD_ERR_OOM, "request larger than the memory budget");

@@ -12,6 +12,7 @@
 // decides acceptance (no wave function here).
 #include "energy_items.cuh"
 #include "move_items.cuh"
+#include "move_tiered.cuh"
 #include "serve.h"
 
 namespace ewald {
@@ -32,7 +33,8 @@ __device__ inline void cta_copy_words(T *dst, const T *src) {
     for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
 }
 
-template <typename R>
+// TIER (R = double): the tiered FP64 form, dE by tiered_delta_e.
+template <typename R, bool TIER>
 __global__ void __launch_bounds__(kMoveThreads, kServeMinBlocks) k_serve_step(ServeDev sv) {
     extern __shared__ __align__(32) unsigned char smem[];
     __shared__ SysDev ss;
@@ -58,9 +60,12 @@ __global__ void __launch_bounds__(kMoveThreads, kServeMinBlocks) k_serve_step(Se
         }
         const int w = d.y, dim = ss.dim;
         MoveSmem<R> m;
-        m.carve_split(smem, smem + sv.img_bytes, ss, dim);
+        TieredMoveSmem tm;
+        if constexpr (TIER) tm.carve_split(smem, smem + sv.img_bytes, ss, dim);
+        else m.carve_split(smem, smem + sv.img_bytes, ss, dim);
         if (s_img_sys != sl.sys) {  // uniform over the CTA
-            m.ims.stage(ss, dim);
+            if constexpr (TIER) tm.stage(ss, dim);
+            else m.ims.stage(ss, dim);
             __syncthreads();
             if (threadIdx.x == 0) s_img_sys = sl.sys;
         }
@@ -109,27 +114,47 @@ __global__ void __launch_bounds__(kMoveThreads, kServeMinBlocks) k_serve_step(Se
         }
         __syncthreads();
         const int k = s_k;
-        Part<R> pold, pnew;
-        for (int q = 0; q < 3; ++q) {
-            pold.u[q] = FP<R>::from64(s_uold[q]);
-            pnew.u[q] = FP<R>::from64(s_unew[q]);
-            set_lo<R>(pold, q, s_uold[q]);
-            set_lo<R>(pnew, q, s_unew[q]);
+        const R qk = FP<R>::q_mob(ss, k);
+        double de;
+        if constexpr (TIER) {
+            const unsigned long long uo[3] = {s_uold[0], s_uold[1], s_uold[2]};
+            const unsigned long long un[3] = {s_unew[0], s_unew[1], s_unew[2]};
+            Part<float> po, pn;
+            if (dim == 3) {
+                tiered_move_parts<3>(ss, k, uo, un, po, pn);
+                build_move_tables<double, 3>(ss, uo, un, tm.tab);
+            } else {
+                tiered_move_parts<2>(ss, k, uo, un, po, pn);
+                build_move_tables<double, 2>(ss, uo, un, tm.tab);
+            }
+            __syncthreads();
+            de = dim == 3 ? tiered_delta_e<3>(ss, sl.b, w, k, po, pn, tm) : tiered_delta_e<2>(ss, sl.b, w, k, po, pn, tm);
+        } else {
+            Part<R> pold, pnew;
+            for (int q = 0; q < 3; ++q) {
+                pold.u[q] = FP<R>::from64(s_uold[q]);
+                pnew.u[q] = FP<R>::from64(s_unew[q]);
+                set_lo<R>(pold, q, s_uold[q]);
+                set_lo<R>(pnew, q, s_unew[q]);
+            }
+            pold.q = pnew.q = qk;
+            if (dim == 2) {  // after the coordinates: the FP64 height shares the third word
+                const R z = ss.n_layers > 1 ? FP<R>::z_mob(ss, k) : R(0);
+                set_part_z(pold, z);
+                set_part_z(pnew, z);
+            }
+            if (dim == 3) build_move_tables<R, 3>(ss, pold.u, pnew.u, m.tab);
+            else build_move_tables<R, 2>(ss, pold.u, pnew.u, m.tab);
+            __syncthreads();
+            de = dim == 3 ? move_delta_e<R, 3>(ss, sl.b, w, k, pold, pnew, m)
+                          : move_delta_e<R, 2>(ss, sl.b, w, k, pold, pnew, m);
         }
-        pold.q = pnew.q = FP<R>::q_mob(ss, k);
-        if (dim == 2) {  // after the coordinates: the FP64 height shares the third word
-            const R z = ss.n_layers > 1 ? FP<R>::z_mob(ss, k) : R(0);
-            set_part_z(pold, z);
-            set_part_z(pnew, z);
-        }
-        if (dim == 3) build_move_tables<R, 3>(ss, pold.u, pnew.u, m.tab);
-        else build_move_tables<R, 2>(ss, pold.u, pnew.u, m.tab);
-        __syncthreads();
-        const double de = dim == 3 ? move_delta_e<R, 3>(ss, sl.b, w, k, pold, pnew, m)
-                                   : move_delta_e<R, 2>(ss, sl.b, w, k, pold, pnew, m);
         if (s_acc) {  // uniform over the CTA
-            if (dim == 3) move_apply_rho<R, 3>(ss, sl.b, w, k, pold.q, m);
-            else move_apply_rho<R, 2>(ss, sl.b, w, k, pold.q, m);
+            const MoveTables<R> *tab;
+            if constexpr (TIER) tab = &tm.tab;
+            else tab = &m.tab;
+            if (dim == 3) move_apply_rho<R, 3>(ss, sl.b, w, k, qk, *tab);
+            else move_apply_rho<R, 2>(ss, sl.b, w, k, qk, *tab);
             __syncthreads();
             if (threadIdx.x < dim) sl.b.u[((size_t)w * dim + threadIdx.x) * ss.mob_stride + k] = s_unew[threadIdx.x];
             if (threadIdx.x == 0) {
@@ -151,20 +176,33 @@ __global__ void __launch_bounds__(kMoveThreads, kServeMinBlocks) k_serve_step(Se
     }
 }
 
+// precision: EWALD_FP64, EWALD_MIXED or EWALD_FP64_TIERED (the tiered
+// kernel; its in-kernel re-sums are the FP64 structure factor's)
 size_t serve_smem(const std::vector<SysDev> &sys, int precision, size_t *img_bytes) {
     size_t img = 0, work = 0;
     for (const SysDev &s : sys) {
-        if (precision == EWALD_FP64) {
+        if (precision == EWALD_FP64_TIERED) {
+            img = std::max(img, TieredMoveSmem::img_bytes(s));
+            work = std::max(work, TieredMoveSmem::work_bytes(s));
+        } else if (precision == EWALD_FP64) {
             img = std::max(img, ImageSmem<double>::bytes(s, s.dim));
             work = std::max(work, MoveSmem<double>::bytes(s) - ImageSmem<double>::bytes(s, s.dim));
         } else {
             img = std::max(img, ImageSmem<float>::bytes(s, s.dim));
             work = std::max(work, MoveSmem<float>::bytes(s) - ImageSmem<float>::bytes(s, s.dim));
         }
-        work = std::max(work, sfac_bytes(s, precision, s.sfac_te, kMoveThreads));
+        const int sp = precision == EWALD_MIXED ? EWALD_MIXED : EWALD_FP64;
+        work = std::max(work, sfac_bytes(s, sp, s.sfac_te, kMoveThreads));
     }
     *img_bytes = img;
     return img + work;
+}
+
+template <typename R, bool TIER>
+static cudaError_t configure_one(size_t smem, int *occ) {
+    cudaError_t e = allow_max_smem(k_serve_step<R, TIER>, smem);
+    if (e) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_serve_step<R, TIER>, kMoveThreads, smem);
 }
 
 int configure_serve(int precision, size_t smem, int *grid) {
@@ -172,13 +210,9 @@ int configure_serve(int precision, size_t smem, int *grid) {
     cudaError_t e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e) return e;
-    if (precision == EWALD_FP64) {
-        if ((e = allow_max_smem(k_serve_step<double>, smem))) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve_step<double>, kMoveThreads, smem);
-    } else {
-        if ((e = allow_max_smem(k_serve_step<float>, smem))) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve_step<float>, kMoveThreads, smem);
-    }
+    if (precision == EWALD_FP64_TIERED) e = configure_one<double, true>(smem, &occ);
+    else if (precision == EWALD_FP64) e = configure_one<double, false>(smem, &occ);
+    else e = configure_one<float, false>(smem, &occ);
     if (e) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     *grid = sms * occ;
@@ -188,8 +222,9 @@ int configure_serve(int precision, size_t smem, int *grid) {
 int launch_serve_step(const ServeDev &d, int precision, int grid, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(d.next, 0, sizeof(int), st);
     if (e) return e;
-    if (precision == EWALD_FP64) k_serve_step<double><<<grid, kMoveThreads, smem, st>>>(d);
-    else k_serve_step<float><<<grid, kMoveThreads, smem, st>>>(d);
+    if (precision == EWALD_FP64_TIERED) k_serve_step<double, true><<<grid, kMoveThreads, smem, st>>>(d);
+    else if (precision == EWALD_FP64) k_serve_step<double, false><<<grid, kMoveThreads, smem, st>>>(d);
+    else k_serve_step<float, false><<<grid, kMoveThreads, smem, st>>>(d);
     return cudaGetLastError();
 }
 

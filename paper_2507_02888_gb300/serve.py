@@ -44,8 +44,8 @@ def _lib():
 class Server:
     def __init__(self, precision="mixed", max_walkers=65536, hbm_budget_bytes=0.0, stream=None):
         lib = _lib()
-        # a tiered FP64 context serves as FP64 (its moves are FP64)
-        prec = {"fp64": ewald.EWALD_FP64, "mixed": ewald.EWALD_MIXED, "fp64_tiered": ewald.EWALD_FP64}[precision]
+        prec = {"fp64": ewald.EWALD_FP64, "mixed": ewald.EWALD_MIXED,
+                "fp64_tiered": ewald.EWALD_FP64_TIERED}[precision]
         h = _vp()
         st = None if stream is None else _vp(stream if isinstance(stream, int) else stream.cuda_stream)
         code = lib.ewald_server_create(prec, int(max_walkers), float(hbm_budget_bytes), st, ctypes.byref(h))

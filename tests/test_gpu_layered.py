@@ -217,7 +217,7 @@ def test_argument_checks(ew):
         ew.context_for(w, mobile_z=w["z"] * 1e5)                    # |dz| g_c beyond 600
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
 def test_served_layered_moves_match_oracle(ew, prec):
     """The serving kernel's device-drawn moves on a bilayer, replayed on the
     host (SplitMix64 + Box-Muller, as in the in-plane serving test) with the

@@ -16,7 +16,7 @@ from paper_2507_02888_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-6}
+TOL = {"fp64": 1e-12, "mixed": 1e-6, "fp64_tiered": 1e-12}
 MASK = (1 << 64) - 1
 
 
@@ -80,7 +80,7 @@ def run_until_done(srv, ids, extra=None, limit=20000):
     raise AssertionError("requests did not finish")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
 def test_request_alone_equals_in_mix(mods, prec):
     ewald, serve = mods
     wa = I.workload("heg3d_sc_n54", 6)
@@ -108,7 +108,7 @@ def test_request_alone_equals_in_mix(mods, prec):
     assert 0 < n_mix.sum() < 25 * 6
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
 @pytest.mark.parametrize("case", ["sc54", "hex60"])
 def test_served_moves_match_oracle(mods, case, prec):
     ewald, serve = mods
@@ -142,6 +142,28 @@ def test_served_moves_match_oracle(mods, case, prec):
         assert n_gpu[walker] == n_acc
         assert abs(e_gpu[walker] - e) <= 2 * TOL[prec] * floor, (walker, e_gpu[walker], e)
         assert abs(e - e_final) <= 1e-10 * floor             # the oracle's own bookkeeping
+
+
+def test_server_precision_must_match_context(mods):
+    """A tiered server takes tiered contexts only; an FP64 server takes FP64
+    and tiered ones (moving them with the plain FP64 kernel)."""
+    ewald, serve = mods
+    w = I.workload("heg3d_sc_n54", 2)
+    c64 = ewald.context_for(w, precision="fp64")
+    ct = ewald.context_for(w, precision="fp64_tiered")
+    cm = ewald.context_for(w, precision="mixed")
+    tiered = serve.Server("fp64_tiered", max_walkers=8)
+    for c in (c64, cm):
+        with pytest.raises(ewald.EwaldError) as ei:
+            tiered.submit(c, w["pos"], 2, 0.3, 0.5, seed=1)
+        assert ei.value.code == 1
+    r = tiered.submit(ct, w["pos"], 4, 0.3, 0.5, seed=1)
+    e_t, n_t, _ = run_until_done(tiered, [r])[r]
+    plain = serve.Server("fp64", max_walkers=8)
+    r = plain.submit(ct, w["pos"], 4, 0.3, 0.5, seed=1)
+    e_p, n_p, _ = run_until_done(plain, [r])[r]
+    assert np.array_equal(n_t, n_p)
+    assert np.max(np.abs(e_t - e_p)) <= 1e-12 * np.max(np.abs(e_p))
 
 
 def test_admission_respects_walker_budget(mods):
