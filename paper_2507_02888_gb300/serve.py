@@ -1,5 +1,5 @@
 """Thin binding of the serving entry points (ewald_server_* in include/ewald.h)
-and a driver for a Poisson stream of requests.
+and a host loop that feeds a Poisson stream of requests to a server.
 
 The request loop itself - admission by walker slots and device memory,
 one persistent launch per step for every active request, retirement - runs
