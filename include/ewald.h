@@ -359,6 +359,16 @@ int ewald_jastrow_u(ewald_batch *b, double *j_out, double *grad_out, double *lap
  * Sec. 4). */
 int ewald_measure_peaks(double *fp32_tflops, double *fp64_tflops, double *mufu_tops);
 
+/* The mixed form's FP32 real-space term erfc(alpha r)/r (Eq. (3), second
+ * term) for n values of r^2 (host arrays, r2[i] > 0 and finite), evaluated
+ * on the GPU by the scalar function and by its paired form (two terms per
+ * lane with FFMA2/FADD2/FMUL2) into scalar_out[n] and paired_out[n].  The
+ * real-space kernels use the paired form; the two are meant to agree bit
+ * for bit.  A diagnostic for tests: synchronous, allocates and frees its
+ * own device buffers.  EWALD_ERR_ARG for n < 0, null arrays, alpha not
+ * positive and finite or an r^2 that is not. */
+int ewald_pair_terms(int n, const float *r2, double alpha, float *scalar_out, float *paired_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,7 @@ SIGNATURES = [
     ("ewald_set_timing", _c_int, [_vp, _c_int]),
     ("ewald_get_timing", _c_int, [_vp, _vp, _vp]),
     ("ewald_measure_peaks", _c_int, [_vp, _vp, _vp]),
+    ("ewald_pair_terms", _c_int, [_c_int, _vp, _c_double, _vp, _vp]),
     ("ewald_jastrow_p_set", _c_int, [_vp, _c_int, _vp]),
     ("ewald_jastrow_p_count", _c_int, [_vp, ctypes.POINTER(_c_int)]),
     ("ewald_jastrow_p", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
@@ -415,6 +416,16 @@ def measure_peaks():
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(_lib.ewald_measure_peaks(ctypes.addressof(a), ctypes.addressof(b), ctypes.addressof(c)))
     return {"fp32_tflops": a.value, "fp64_tflops": b.value, "rsqrt_tops": c.value}
+
+
+def pair_terms(r2, alpha):
+    """The FP32 term erfc(alpha r)/r for float32 r^2 values on the GPU: (scalar, paired) float32 arrays."""
+    load()
+    r2 = np.ascontiguousarray(r2, dtype=np.float32)
+    sc = np.empty_like(r2)
+    pa = np.empty_like(r2)
+    _check(_lib.ewald_pair_terms(int(r2.size), r2.ctypes.data, float(alpha), sc.ctypes.data, pa.ctypes.data))
+    return sc, pa
 
 
 def tune_alpha(dim, lattice, mobile_charge, pos, fixed_pos=None, fixed_charge=None, alpha=0.0, precision="fp64",
