@@ -368,6 +368,12 @@ int ewald_measure_peaks(double *fp32_tflops, double *fp64_tflops, double *mufu_t
  * own device buffers.  EWALD_ERR_ARG for n < 0, null arrays, alpha not
  * positive and finite or an r^2 that is not. */
 int ewald_pair_terms(int n, const float *r2, double alpha, float *scalar_out, float *paired_out);
+/* The tiered form's head-term arithmetic (double-float 1/r by Newton steps,
+ * piecewise-Taylor erfc; FP32 pipe only) on n FP64 values of r^2 (host
+ * arrays), erfc(alpha r)/r returned in FP64 in out[n].  Same diagnostic
+ * terms and errors as ewald_pair_terms; alpha r must stay below 4, the
+ * head range (erfc(alpha r) > 1e-7 means alpha r < 3.77). */
+int ewald_pair_terms_df(int n, const double *r2, double alpha, double *out);
 
 #ifdef __cplusplus
 }

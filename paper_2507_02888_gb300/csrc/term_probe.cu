@@ -1,7 +1,8 @@
-// Diagnostic entry point: the mixed form's FP32 real-space term
-// erfc(alpha r)/r (paper Eq. (3), second term) evaluated by the scalar
-// function and by its paired (two terms per lane) form, for the tests that
-// pin its accuracy against FP64 and the two forms against each other.
+// Diagnostic entry points: the real-space term erfc(alpha r)/r (paper Eq.
+// (3), second term) as the kernels evaluate it - the mixed form's FP32
+// function, scalar and paired (two terms per lane), and the tiered form's
+// double-float head-term arithmetic - for the tests that pin their accuracy
+// against FP64 and the two FP32 forms against each other.
 #include <cmath>
 
 #include "../../include/ewald.h"
@@ -26,7 +27,39 @@ __global__ void k_pair_terms(int n, const float *__restrict__ r2, TermK32 k, flo
     }
 }
 
+// The tiered form's head-term arithmetic on r^2 alone: erfc(alpha r)/r in
+// double-float (df_rsqrt, df_erfc; df_math.cuh), returned in FP64.
+__global__ void k_pair_terms_df(int n, const double *__restrict__ r2, float a_hi, float a_lo,
+                                double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const DF q = df_from(r2[i]);
+    const DF rinv = df_rsqrt(q);
+    const DF x = df_mul(DF{a_hi, a_lo}, df_mul(q, rinv));
+    out[i] = df_to(df_mul(df_erfc(x), rinv));
+}
+
 }  // namespace
+
+extern "C" int ewald_pair_terms_df(int n, const double *r2, double alpha, double *out) {
+    if (n < 0 || (n > 0 && (!r2 || !out)) || !(alpha > 0) || !std::isfinite(alpha)) return EWALD_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!(r2[i] > 0) || !std::isfinite(r2[i])) return EWALD_ERR_ARG;
+    if (n == 0) return EWALD_OK;
+    const float a_hi = (float)alpha, a_lo = (float)(alpha - (double)a_hi);
+    double *d = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)n;
+    cudaError_t e = cudaMalloc((void **)&d, 2 * bytes);
+    if (e) return e == cudaErrorMemoryAllocation ? EWALD_ERR_OOM : EWALD_ERR_CUDA;
+    e = cudaMemcpy(d, r2, bytes, cudaMemcpyHostToDevice);
+    if (!e) {
+        k_pair_terms_df<<<(n + 255) / 256, 256>>>(n, d, a_hi, a_lo, d + n);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpy(out, d + n, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e ? EWALD_ERR_CUDA : EWALD_OK;
+}
 
 extern "C" int ewald_pair_terms(int n, const float *r2, double alpha, float *scalar_out, float *paired_out) {
     if (n < 0 || (n > 0 && (!r2 || !scalar_out || !paired_out)) || !(alpha > 0) || !std::isfinite(alpha))

@@ -98,6 +98,7 @@ SIGNATURES = [
     ("ewald_get_timing", _c_int, [_vp, _vp, _vp]),
     ("ewald_measure_peaks", _c_int, [_vp, _vp, _vp]),
     ("ewald_pair_terms", _c_int, [_c_int, _vp, _c_double, _vp, _vp]),
+    ("ewald_pair_terms_df", _c_int, [_c_int, _vp, _c_double, _vp]),
     ("ewald_jastrow_p_set", _c_int, [_vp, _c_int, _vp]),
     ("ewald_jastrow_p_count", _c_int, [_vp, ctypes.POINTER(_c_int)]),
     ("ewald_jastrow_p", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
@@ -426,6 +427,15 @@ def pair_terms(r2, alpha):
     pa = np.empty_like(r2)
     _check(_lib.ewald_pair_terms(int(r2.size), r2.ctypes.data, float(alpha), sc.ctypes.data, pa.ctypes.data))
     return sc, pa
+
+
+def pair_terms_df(r2, alpha):
+    """The tiered form's double-float erfc(alpha r)/r for FP64 r^2 values on the GPU, as FP64."""
+    load()
+    r2 = np.ascontiguousarray(r2, dtype=np.float64)
+    out = np.empty_like(r2)
+    _check(_lib.ewald_pair_terms_df(int(r2.size), r2.ctypes.data, float(alpha), out.ctypes.data))
+    return out
 
 
 def tune_alpha(dim, lattice, mobile_charge, pos, fixed_pos=None, fixed_charge=None, alpha=0.0, precision="fp64",

@@ -68,3 +68,32 @@ def test_pair_terms_arguments(ew):
         ew.pair_terms(np.array([1.0], dtype=np.float32), -1.0)
     sc, pa = ew.pair_terms(np.zeros(0, dtype=np.float32), 0.5)
     assert sc.size == 0 and pa.size == 0
+
+
+@pytest.mark.parametrize("alpha", [0.15685, 0.4595])
+def test_double_float_head_term_against_fp64(ew, alpha):
+    """The tiered form's head-term arithmetic (double-float 1/r and erfc,
+    FP32 pipe only) on the head range x = alpha r < 3.77 against the FP64
+    definition.  Bound per term 2e-14 (1 + 2 x^2): the pairs carry 48 bits,
+    so x = alpha r (alpha itself a float pair) is good to ~1e-14, and
+    erfc(x) turns a relative error e of x into ~2 x^2 e (measured: 1.2e-14
+    near x = 0 to 4.0e-13 at x = 3.6).  The magnitude-weighted mean error,
+    which is what a sum of head terms sees, stays below 5e-15."""
+    rng = np.random.default_rng(7)
+    x = np.concatenate([3.77 * rng.random(200000) ** (1 / 3), np.exp(rng.uniform(np.log(1e-3), np.log(3.77), 50001))])
+    r2 = (x / alpha) ** 2
+    got = ew.pair_terms_df(r2, alpha)
+    r = np.sqrt(r2)
+    ref = special.erfc(alpha * r) / r
+    rel = (got - ref) / ref
+    vol = slice(0, 200000)                             # the volume-weighted part
+    wbias = np.sum(got[vol] - ref[vol]) / np.sum(ref[vol])
+    print("alpha %g: max |rel| %.3e, weighted mean %.3e" % (alpha, np.max(np.abs(rel)), wbias))
+    assert np.all(np.abs(rel) <= 2e-14 * (1 + 2 * x ** 2))
+    assert abs(wbias) <= 5e-15
+
+
+def test_pair_terms_df_arguments(ew):
+    with pytest.raises(ew.EwaldError):
+        ew.pair_terms_df(np.array([1.0, -2.0]), 0.5)
+    assert ew.pair_terms_df(np.zeros(0), 0.5).size == 0
