@@ -132,24 +132,44 @@ def oracle_walker_energies(w, walkers, rc, gc, threads):
         return list(ex.map(one, range(len(walkers))))
 
 
+def cpu_model():
+    """Host CPU model name (lscpu; /proc/cpuinfo as a fallback), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_oracle_rate(w, rc, gc, seconds):
-    """Walker energies/s of the oracle on all host cores, on a bounded sample."""
+    """Walker energies/s of the oracle on one host thread and on all host
+    cores (one walker per thread at a time), on bounded samples."""
     import oracle
     cores = host_cores()
     oracle.build()
+    oracle_walker_energies(w, [0], rc, gc, 1)          # load the library outside the timing
     t0 = time.perf_counter()
-    oracle_walker_energies(w, [0], rc, gc, 1)
-    t1 = time.perf_counter() - t0
-    per_round = t1  # one walker per core per round
-    rounds = max(1, min(4, int(seconds / max(per_round, 1e-3))))
+    oracle_walker_energies(w, [1, 2], rc, gc, 1)
+    t1 = (time.perf_counter() - t0) / 2                  # one walker on one thread
+    rounds = max(1, min(4, int(seconds / max(t1, 1e-3))))
     n = cores * rounds
     walkers = [i % w["n_walkers"] for i in range(n)]
     t0 = time.perf_counter()
     oracle_walker_energies(w, walkers, rc, gc, cores)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "walker energies/s", "cores": cores, "kind": "oracle",
-            "sample": "%d walkers of %s (%d per host thread), plain FP64 C oracle, %.1f s wall"
-                      % (n, w["name"], rounds, dt)}
+            "one_thread": 1.0 / t1, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "sample": "%d walkers of %s (%d per host thread) on %d threads, plain FP64 C oracle, %.1f s wall; "
+                      "one thread: 2 walkers, %.2f s each" % (n, w["name"], rounds, cores, dt, t1)}
 
 
 # ------------------------------------------------------------------- our arm
@@ -205,6 +225,18 @@ def move_roofline(info, w, W, moves_per_s, accept_frac, peaks, hbm_peak, hbm_bas
     return {"bytes_per_move": bytes_move, "achieved_gbs": gbs, "hbm_peak_gbs": hbm_peak,
             "hbm_frac": gbs / hbm_peak, "hbm_basis": hbm_basis, "flop_per_move": flop_move,
             "achieved_tflops": tf, "fp32_frac_of_measured": tf / peaks["fp32_tflops"]}
+
+
+def de_stats(de, de_fp64, floor):
+    """A form's move dE against the FP64 path's, every walker: relative to
+    the walker's floor max(|E|, 1e-2 S) and to |dE| itself."""
+    d = np.abs(de - de_fp64)
+    rel = d / np.maximum(np.abs(de_fp64), 1e-300)
+    return {"walkers": int(d.size), "abs_max_ha": float(np.max(d)), "abs_median_ha": float(np.median(d)),
+            "vs_walker_floor_max": float(np.max(d / floor)),
+            "vs_abs_de_median": float(np.median(rel)), "vs_abs_de_p99": float(np.percentile(rel, 99)),
+            "vs_abs_de_max": float(np.max(rel)), "frac_within_1e-6_of_abs_de": float(np.mean(rel <= 1e-6)),
+            "abs_de_median_ha": float(np.median(np.abs(de_fp64)))}
 
 
 def ranks_max(vals, world):
@@ -292,6 +324,14 @@ def run_ours(args, rank, world, local_rank):
     def max_over_ranks(vals):
         return ranks_max(vals, world)
 
+    def first_round_de(b):
+        """dE of every walker's first move from the workload's configuration
+        (before any step: every move proposes a real displacement)."""
+        with torch.cuda.stream(stream):
+            b.propose(k_d[0], rn_d[0], de_d[0])
+            torch.cuda.synchronize()
+        return de_d[0].cpu().numpy().copy()
+
     # measured arithmetic peaks (a few ms, before any timed region)
     peaks = ewald.measure_peaks()
     hbm_peak, hbm_basis = measured_hbm()
@@ -299,6 +339,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- mixed precision, batched: the headline
     ctx, b = make("mixed")
     info = ctx.info()
+    de0_mixed = first_round_de(b)
     props = torch.cuda.get_device_properties(dev)
     bus = ("%02x:%02x.0" % (props.pci_bus_id, props.pci_device_id)
            if isinstance(getattr(props, "pci_bus_id", None), int) else "")
@@ -374,6 +415,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- plain FP64 form, same workload
     if not args.no_fp64:
         ctx, b = make("fp64")
+        de0_fp64 = first_round_de(b)
         fs = max(1, args.fp64_steps)
         f_e, f_m, f_t, _ = timed_steps(b, ctx, fs, 1, M)
         f_e, f_m = max_over_ranks([f_e, f_m])
@@ -387,7 +429,8 @@ def run_ours(args, rank, world, local_rank):
         result["accuracy"] = {"mixed_vs_fp64_max": float(np.max(np.abs(rel))), "mixed_vs_fp64_mean": float(np.mean(rel)),
                               "gate": 1e-6, "walkers": int(W),
                               "measure": "|E_mixed - E_fp64| / max(|E|, 1e-2 S) per walker; the FP64 path "
-                                         "(cutoffs at 1e-16) is within 1e-12 of the oracle"}
+                                         "(cutoffs at 1e-16) is within 1e-12 of the oracle",
+                              "move_de_mixed": de_stats(de0_mixed, de0_fp64, floor)}
         i64 = ctx.info()
         r64_ms, r64_n = f_t["real"]
         a64 = expected_real_terms(i64, w) * W * FLOP_REAL_TERM / (r64_ms / r64_n / 1e3) / 1e12
@@ -406,10 +449,12 @@ def run_ours(args, rank, world, local_rank):
         # ---- tiered FP64 form: FP64 results, the real-space images below
         # erfc(alpha r) = 1e-7 in FP32 (EWALD_FP64_TIERED)
         ctx, b = make("fp64_tiered")
+        de0_tiered = first_round_de(b)
         g_e, g_m, g_t, _ = timed_steps(b, ctx, fs, 1, M)
         g_e, g_m = max_over_ranks([g_e, g_m])
         rel_g = (e_d.cpu().numpy() - e_fp64) / floor
         rel_de = (de_d.cpu().numpy() - de_fp64) / floor[None, :] if M else np.zeros(1)
+        result["accuracy"]["move_de_fp64_tiered"] = de_stats(de0_tiered, de0_fp64, floor)
         result["fp64_tiered"] = {"value": world * W * fs / (g_e / 1e3), "unit": "walker energies/s",
                                  "moves": world * W * M * fs / (g_m / 1e3) if M else None,
                                  "steps": fs, "vs_fp64_max": float(np.max(np.abs(rel_g))),
@@ -503,6 +548,33 @@ def run_ours(args, rank, world, local_rank):
         sv["fp64"] = run_serving(stream, "fp64", args.serve_requests_fp64)
         sv["fp64_tiered"] = run_serving(stream, "fp64_tiered", args.serve_requests_tiered)
         result["serving"] = sv
+
+    # ---- the numbers that qualify the headline, on the objects of the line
+    # that carry the measurement (roofline) and the workload (config)
+    rf = result["roofline"]
+    mv = result["moves"]["roofline"]
+    if mv:
+        rf["moves"] = {"bound": "hbm", "kernels": "k_propose + k_accept", "achieved": mv["achieved_gbs"],
+                       "peak": hbm_peak, "unit": "GB/s", "frac": mv["hbm_frac"], "peak_basis": hbm_basis,
+                       "bytes_per_move": mv["bytes_per_move"], "moves_per_s": moves_per_s,
+                       "fp32_frac_of_measured": mv["fp32_frac_of_measured"]}
+    if "mixed_at_fp64_cutoff" in result and "fp64" in result:
+        eq = result["mixed_at_fp64_cutoff"]
+        rf["equal_cutoff"] = {"mixed_value": eq["value"], "fp64_value": result["fp64"]["value"],
+                              "mixed_over_fp64": eq["value"] / result["fp64"]["value"],
+                              "real_frac": eq["real_frac"], "r_cutoff": eq["r_cutoff"],
+                              "unit": "walker energies/s", "note": "both forms at erfc(alpha r_c) = 1e-16"}
+    if "accuracy" in result:
+        a = result["accuracy"]
+        acc_cfg = {"energy_mixed_vs_fp64_max": a["mixed_vs_fp64_max"], "gate": a["gate"],
+                   "measure": "relative to max(|E|, 1e-2 S) per walker, all walkers"}
+        for key in ("move_de_mixed", "move_de_fp64_tiered"):
+            if key in a:
+                acc_cfg[key] = {k: a[key][k] for k in ("vs_walker_floor_max", "vs_abs_de_median", "vs_abs_de_p99",
+                                                      "vs_abs_de_max", "abs_max_ha")}
+        if "fp64_tiered" in result:
+            acc_cfg["energy_fp64_tiered_vs_fp64_max"] = result["fp64_tiered"]["vs_fp64_max"]
+        result["config"]["accuracy"] = acc_cfg
 
     # ---- CPU oracle on the host cores (rank 0 only)
     if rank == 0 and not args.no_cpu_baseline and world == 1:

@@ -63,7 +63,8 @@ enum {
     EWALD_ERR_OOM = 5,         /* device or host allocation failed, or over the memory budget */
     EWALD_ERR_CUDA = 6,        /* a CUDA runtime call failed */
     EWALD_ERR_TIMEOUT = 7,     /* a bounded device-side wait expired */
-    EWALD_ERR_STATE = 8        /* call not valid in the object's current state */
+    EWALD_ERR_STATE = 8,       /* call not valid in the object's current state */
+    EWALD_ERR_CANCELLED = 9    /* the serving request was cancelled (ewald_server_cancel) */
 };
 
 typedef struct {
@@ -234,14 +235,31 @@ int ewald_server_submit(ewald_server *srv, ewald_ctx *system, const double *pos,
  * active request; returns without waiting for the device. */
 int ewald_server_step(ewald_server *srv, int *n_active, int *n_queued);
 /* EWALD_OK and the results (host arrays [W], either may be NULL) once the
- * request is done, EWALD_ERR_STATE before; latency_ms = submission to
- * completion as seen by the host. */
+ * request is done, EWALD_ERR_STATE before, EWALD_ERR_CANCELLED after
+ * ewald_server_cancel; latency_ms = submission to completion as seen by the
+ * host. */
 int ewald_server_result(ewald_server *srv, int request_id, double *energies, int *n_accepted,
                         double *latency_ms);
 /* Ids of requests that finished since the last call (up to max_ids, the
  * rest on the next call; *n receives the count): a host loop can fetch just
  * those results instead of polling every pending request. */
 int ewald_server_completed(ewald_server *srv, int *ids, int max_ids, int *n);
+/* Device bytes that admission counts against the server's memory budget
+ * for a request of n_walkers walkers of system (its batch state and
+ * upload buffer), in *bytes.  A request above the budget is refused by
+ * ewald_server_submit with EWALD_ERR_OOM; queued requests wait until the
+ * bytes of the active ones plus theirs fit.  Not in the paper. */
+int ewald_server_request_bytes(const ewald_ctx *system, int n_walkers, double *bytes);
+/* Cancel a request from the host.  A queued request leaves the queue; an
+ * active one stops moving: it is retired at the next ewald_server_step
+ * (its device memory returned, stream-ordered, after the moves already
+ * queued), without results.  Either way it is reported once by
+ * ewald_server_completed, and ewald_server_result answers
+ * EWALD_ERR_CANCELLED.  The other requests are unaffected (every walker's
+ * result is the same alone and in any mix).  EWALD_ERR_STATE if the request
+ * has already finished or was cancelled; EWALD_ERR_ARG for an unknown id.
+ * Not in the paper: a serving-loop facility. */
+int ewald_server_cancel(ewald_server *srv, int request_id);
 /* Wait until everything queued on the server's stream has run. */
 int ewald_server_drain(ewald_server *srv);
 const char *ewald_server_error_message(const ewald_server *srv);
@@ -282,8 +300,10 @@ int ewald_tune_alpha(const ewald_desc *desc, void *cuda_stream, int n_walkers, c
 
 /* Full energies without any device allocation at call time.  Meant for
  * callers that cannot call cudaMalloc while they compute (a host framework
- * that owns all device memory through its own pool, a CUDA-graph capture
- * that must not allocate, an embedded code that reserves memory up front).
+ * that owns all device memory through its own pool and would see a foreign
+ * allocation fragment it, an embedded code that reserves memory up front).
+ * Every precision form of the context computes what ewald_energy computes
+ * (the tiered form with its double-float structure factor).
  * pos [n_walkers][N][dim] and e_out [n_walkers] are device arrays of the
  * caller; status_out (device int, may be NULL) receives 0, or bit 1 for
  * coincident particles and bit 4 for a non-finite position.  All

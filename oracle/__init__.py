@@ -53,6 +53,8 @@ def _load():
             lib.oracle_energy.argtypes = [c_int, dp, c_int, dp, dp, c_double, c_double, c_double, dp, dp]
             lib.oracle_delta_e.argtypes = [c_int, dp, c_int, dp, dp, c_int, dp, c_double, c_double,
                                            c_double, dp]
+            lib.oracle_delta_e_parts.argtypes = [c_int, dp, c_int, dp, dp, c_int, dp, c_double, c_double,
+                                                 c_double, dp, dp]
             lib.oracle_rho_at.argtypes = [c_int, dp, c_int, dp, dp, c_int, ip, dp]
             lib.oracle_recip_pairsum.argtypes = [c_int, dp, c_int, dp, dp, c_double, c_double, dp]
             lib.oracle_gcount.argtypes = [c_int, dp, c_double]
@@ -69,7 +71,7 @@ def _load():
             lib.oracle_jastrow_u.restype = ctypes.c_int
             lib.oracle_jastrow_stars.restype = ctypes.c_int
             lib.oracle_jastrow_p.restype = ctypes.c_int
-            for f in (lib.oracle_energy, lib.oracle_delta_e, lib.oracle_rho_at,
+            for f in (lib.oracle_energy, lib.oracle_delta_e, lib.oracle_delta_e_parts, lib.oracle_rho_at,
                       lib.oracle_recip_pairsum, lib.oracle_cutoffs):
                 f.restype = ctypes.c_int
             _lib = lib
@@ -125,6 +127,20 @@ def delta_e(dim, lattice, pos, q, k, r_new, alpha, r_c, g_c):
     _check(_load().oracle_delta_e(dim, _dp(lat), n, _dp(pos), _dp(q), int(k), _dp(rn), alpha, r_c,
                                   g_c, ctypes.byref(de)))
     return de.value
+
+
+def delta_e_parts(dim, lattice, pos, q, k, r_new, alpha, r_c, g_c):
+    """(dE_real, dE_recip): the real-space and reciprocal-space parts of delta_e."""
+    lat = _f64(lattice, (dim, dim))
+    pos = _f64(pos)
+    n = pos.shape[0]
+    pos = pos.reshape(n, dim)
+    q = _f64(q, (n,))
+    rn = _f64(r_new, (dim,))
+    dr, dk = ctypes.c_double(), ctypes.c_double()
+    _check(_load().oracle_delta_e_parts(dim, _dp(lat), n, _dp(pos), _dp(q), int(k), _dp(rn), alpha, r_c,
+                                        g_c, ctypes.byref(dr), ctypes.byref(dk)))
+    return dr.value, dk.value
 
 
 def rho_at(dim, lattice, pos, q, nvec):

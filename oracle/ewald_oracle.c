@@ -346,12 +346,15 @@ static void visit_move(const double *G, double g, const int *nvec, void *vctx) {
     kadd(&m->sum, recip_weight(m->dim, g, m->alpha) * (after - before));
 }
 
-int oracle_delta_e(int dim, const double *lattice, int n, const double *pos, const double *q,
-                   int k, const double *r_new, double alpha, double r_c, double g_c,
-                   double *de) {
+/* The move's real-space and reciprocal-space parts separately (their sum is
+ * oracle_delta_e's result); the parts set the scale of a move's energy
+ * change against which its rounding is judged. */
+int oracle_delta_e_parts(int dim, const double *lattice, int n, const double *pos, const double *q,
+                         int k, const double *r_new, double alpha, double r_c, double g_c,
+                         double *de_real, double *de_recip) {
     int st = check_common(dim, lattice, n, pos, q, alpha, r_c, g_c);
     if (st) return st;
-    if (k < 0 || k >= n || !r_new || !de) return ORC_ERR_ARG;
+    if (k < 0 || k >= n || !r_new || !de_real || !de_recip) return ORC_ERR_ARG;
     cell_t c;
     if ((st = make_cell(dim, lattice, &c))) return st;
 
@@ -369,7 +372,19 @@ int oracle_delta_e(int dim, const double *lattice, int n, const double *pos, con
     }
     move_ctx mc = {dim, n, k, pos, q, r_new, alpha, {0.0, 0.0}};
     for_each_g(&c, g_c, visit_move, &mc);
-    *de = kval(&d_real) + recip_prefactor(&c) * kval(&mc.sum);
+    *de_real = kval(&d_real);
+    *de_recip = recip_prefactor(&c) * kval(&mc.sum);
+    return ORC_OK;
+}
+
+int oracle_delta_e(int dim, const double *lattice, int n, const double *pos, const double *q,
+                   int k, const double *r_new, double alpha, double r_c, double g_c,
+                   double *de) {
+    if (!de) return ORC_ERR_ARG;
+    double re = 0.0, rc = 0.0;
+    int st = oracle_delta_e_parts(dim, lattice, n, pos, q, k, r_new, alpha, r_c, g_c, &re, &rc);
+    if (st) return st;
+    *de = re + rc;
     return ORC_OK;
 }
 

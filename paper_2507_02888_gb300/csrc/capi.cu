@@ -448,6 +448,7 @@ const char *ewald_strerror(int code) {
         case EWALD_ERR_CUDA: return "CUDA runtime error";
         case EWALD_ERR_TIMEOUT: return "device wait timed out";
         case EWALD_ERR_STATE: return "call not valid in the current state";
+        case EWALD_ERR_CANCELLED: return "request cancelled";
         default: return "unknown error";
     }
 }

@@ -2,9 +2,8 @@
 // device allocation at call time.
 //
 // Some callers cannot call cudaMalloc: code running inside another
-// framework's memory pool that must not fragment it, a CUDA-graph capture
-// that forbids allocation, or an embedded host that reserves all device
-// memory up front.  This entry point takes the walkers' positions and the
+// framework's memory pool that must not fragment it, or an embedded host
+// that reserves all device memory up front.  This entry point takes the walkers' positions and the
 // output array from the caller and keeps every intermediate (fixed-point
 // coordinates, rho(G), partial sums, status word) in one file-scope
 // __device__ array of fixed size, kNoAllocScratchBytes, that every GPU which
@@ -14,6 +13,7 @@
 #include <string>
 
 #include "capi_internal.h"
+#include "sfac_df.h"
 
 namespace ewald {
 
@@ -67,8 +67,10 @@ static size_t carve(const SysDev &s, int W, unsigned char *base, BatchDev *b) {
     return off;
 }
 
-static int noalloc_energy(const SysDev &s, const LaunchCfg &cfg, int precision, const double *pos, int W,
-                   double *e_out, int *status_out, cudaStream_t st) {
+// tiered: an EWALD_FP64_TIERED context (precision EWALD_FP64), whose
+// structure factor is the double-float kernel, as in ewald_energy
+static int noalloc_energy(const SysDev &s, const LaunchCfg &cfg, int precision, bool tiered, const double *pos,
+                          int W, double *e_out, int *status_out, cudaStream_t st) {
     BatchDev b{};
     if (carve(s, W, nullptr, &b) > kNoAllocScratchBytes) return -1;  // too many walkers
     void *base = nullptr;
@@ -79,7 +81,8 @@ static int noalloc_energy(const SysDev &s, const LaunchCfg &cfg, int precision, 
     // the status word is the only scratch that must start at zero
     if ((e = cudaMemsetAsync(b.status, 0, sizeof(int), st))) return e;
     if ((e = launch_ingest(s, b, pos, st))) return e;
-    if ((e = launch_sfac(s, b, precision, cfg, nullptr, st))) return e;
+    if ((e = tiered ? launch_sfac_df(s, b, cfg, nullptr, st) : launch_sfac(s, b, precision, cfg, nullptr, st)))
+        return e;
     if ((e = launch_real(s, b, precision, cfg, st))) return e;
     if ((e = launch_combine(s, b, st))) return e;
     if (status_out && (e = cudaMemcpyAsync(status_out, b.status, sizeof(int), cudaMemcpyDeviceToDevice, st)))
@@ -112,6 +115,6 @@ extern "C" int ewald_energy_noalloc(ewald_ctx *c, const double *pos, int n_walke
                  std::to_string(limit) + " walkers of this system";
         return fail(c, EWALD_ERR_OOM);
     }
-    int e = ewald::noalloc_energy(c->s, c->cfg, c->t.precision, pos, n_walkers, e_out, status_out, c->stream);
+    int e = ewald::noalloc_energy(c->s, c->cfg, c->t.precision, c->t.tiered, pos, n_walkers, e_out, status_out, c->stream);
     return e ? cuda_fail(c, (cudaError_t)e) : EWALD_OK;
 }

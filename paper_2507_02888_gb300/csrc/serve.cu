@@ -39,7 +39,9 @@ double now_s() {
 struct Req {
     int id = 0;
     ewald_ctx *ctx = nullptr;
-    int W = 0, n_steps = 0, sys = -1, slot = -1, steps_done = 0, state = 0;  // 0 queued 1 active 2 draining 3 done
+    // state: 0 queued, 1 active, 2 draining, 3 done, 4 cancelled
+    int W = 0, n_steps = 0, sys = -1, slot = -1, steps_done = 0, state = 0;
+    bool cancel = false;  // active, cancelled by the host: retire at the next step without results
     int acc_base = 0;
     unsigned long long seed = 0;
     double sigma = 0, accept_p = 0;
@@ -378,6 +380,19 @@ int ewald_server_step(ewald_server *s, int *n_active, int *n_queued) {
         int id = s->slot_req[slot];
         if (id < 0) continue;
         Req &r = s->reqs[id];
+        if (r.cancel) {  // memory back to the pool after the moves already queued; no results
+            for (void *p : r.dev) cudaFreeAsync(p, s->stream);
+            r.dev.clear();
+            r.state = 4;
+            r.t_done = now_s();
+            s->completed.push_back(r.id);
+            s->slot_req[slot] = -1;
+            s->used_walkers -= r.W;
+            s->used_bytes -= r.bytes;
+            give_acc_range(s, r.acc_base, r.W);
+            s->items_dirty = true;
+            continue;
+        }
         if (r.steps_done < r.n_steps) continue;
         if (!r.pin_e) {
             if ((e = cudaMallocHost((void **)&r.pin_e, sizeof(double) * r.W))) return srv_cuda(s, e, "result buffer");
@@ -495,6 +510,7 @@ int ewald_server_result(ewald_server *s, int request_id, double *energies, int *
         r.state = 3;
         r.t_done = now_s();
     }
+    if (r.state == 4) return EWALD_ERR_CANCELLED;
     if (r.state != 3) return EWALD_ERR_STATE;
     if (energies) std::memcpy(energies, r.pin_e, sizeof(double) * r.W);
     if (n_accepted) std::memcpy(n_accepted, r.pin_acc, sizeof(int) * r.W);
@@ -509,6 +525,33 @@ int ewald_server_completed(ewald_server *s, int *ids, int max_ids, int *n) {
     s->completed.erase(s->completed.begin(), s->completed.begin() + k);
     *n = k;
     return EWALD_OK;
+}
+
+int ewald_server_request_bytes(const ewald_ctx *system, int n_walkers, double *bytes) {
+    if (!system || n_walkers < 1 || !bytes) return EWALD_ERR_ARG;
+    *bytes = (double)request_bytes(system, n_walkers);
+    return EWALD_OK;
+}
+
+int ewald_server_cancel(ewald_server *s, int request_id) {
+    if (!s) return EWALD_ERR_ARG;
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end()) return srv_fail(s, EWALD_ERR_ARG, "unknown request");
+    Req &r = it->second;
+    if (r.state == 0) {  // queued: nothing on the device yet
+        s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r.id));
+        r.state = 4;
+        r.t_done = now_s();
+        r.pos.clear();
+        r.pos.shrink_to_fit();
+        s->completed.push_back(r.id);
+        return EWALD_OK;
+    }
+    if (r.state == 1 && !r.cancel && r.steps_done < r.n_steps) {
+        r.cancel = true;
+        return EWALD_OK;
+    }
+    return srv_fail(s, EWALD_ERR_STATE, "request already finished or cancelled");
 }
 
 int ewald_server_drain(ewald_server *s) {

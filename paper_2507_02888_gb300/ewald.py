@@ -18,7 +18,7 @@ from . import build as _build
 EWALD_FP64, EWALD_MIXED, EWALD_FP64_TIERED = 0, 1, 2
 PRECISIONS = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED, "fp64_tiered": EWALD_FP64_TIERED}
 ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_LATTICE", 3: "ERR_COINCIDENT", 4: "ERR_NO_PROPOSAL",
-             5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
+             5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_STATE", 9: "ERR_CANCELLED"}
 
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -24,6 +24,8 @@ SIGNATURES = [
     ("ewald_server_result", _c_int, [_vp, _c_int, _vp, _vp, ctypes.POINTER(_c_double)]),
     ("ewald_server_completed", _c_int, [_vp, _vp, _c_int, ctypes.POINTER(_c_int)]),
     ("ewald_server_drain", _c_int, [_vp]),
+    ("ewald_server_cancel", _c_int, [_vp, _c_int]),
+    ("ewald_server_request_bytes", _c_int, [_vp, _c_int, ctypes.POINTER(_c_double)]),
     ("ewald_server_error_message", ctypes.c_char_p, [_vp]),
 ]
 _bound = False
@@ -93,6 +95,10 @@ class Server:
         self._check(code)
         return e, n, lat.value
 
+    def cancel(self, rid):
+        """Cancel a queued or active request (ewald_server_cancel)."""
+        self._check(_lib().ewald_server_cancel(self._h, int(rid)))
+
     def drain(self):
         self._check(_lib().ewald_server_drain(self._h))
 
@@ -106,6 +112,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def request_bytes(ctx, n_walkers):
+    """Device bytes a request of n_walkers walkers of ctx counts against a server's budget."""
+    b = _c_double()
+    code = _lib().ewald_server_request_bytes(ctx._h, int(n_walkers), ctypes.byref(b))
+    if code:
+        raise ewald.EwaldError(code, "request bytes")
+    return b.value
 
 
 def run_stream(server, requests, time_limit=600.0):

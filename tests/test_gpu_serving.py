@@ -194,3 +194,94 @@ def test_admission_respects_walker_budget(mods):
     assert sorted(got) == sorted(ids)
     srv.step()
     assert srv.completed() == []
+
+
+def test_admission_respects_memory_budget(mods):
+    """A device-memory budget that holds one request at a time: the requests
+    queue and run one after another, with the results of an unconstrained
+    server (bit for bit: a walker's result does not depend on the mix)."""
+    ewald, serve = mods
+    w = I.workload("heg3d_sc_n54", 6)
+    ctx = ewald.context_for(w, precision="mixed")
+    need = serve.request_bytes(ctx, 6)
+    assert need > 6 * 54 * 3 * 8                             # at least the positions
+    free = serve.Server("mixed", max_walkers=64)
+    ids_f = [free.submit(ctx, w["pos"], 6, 0.3, 0.5, seed=40 + s) for s in range(3)]
+    res_f = run_until_done(free, ids_f)
+    tight = serve.Server("mixed", max_walkers=64, hbm_budget_bytes=1.5 * need)
+    ids_t = [tight.submit(ctx, w["pos"], 6, 0.3, 0.5, seed=40 + s) for s in range(3)]
+    seen = []
+    out = {}
+    for _ in range(2000):
+        a, q = tight.step()
+        seen.append((a, q))
+        for rid in ids_t:
+            if rid not in out:
+                r = tight.result(rid)
+                if r is not None:
+                    out[rid] = r
+        if len(out) == 3:
+            break
+    assert len(out) == 3
+    assert max(a for a, _ in seen) == 1 and max(q for _, q in seen) == 2   # one at a time, two waiting
+    for rf, rt in zip(ids_f, ids_t):
+        assert np.array_equal(res_f[rf][0], out[rt][0]) and np.array_equal(res_f[rf][1], out[rt][1])
+
+
+def test_request_over_budget_is_refused(mods):
+    ewald, serve = mods
+    w = I.workload("heg3d_sc_n54", 6)
+    ctx = ewald.context_for(w, precision="mixed")
+    need = serve.request_bytes(ctx, 6)
+    srv = serve.Server("mixed", max_walkers=64, hbm_budget_bytes=need - 1)
+    with pytest.raises(ewald.EwaldError) as ei:
+        srv.submit(ctx, w["pos"], 3, 0.3, 0.5, seed=1)
+    assert ei.value.code == 5                                # EWALD_ERR_OOM, nothing queued
+    assert srv.step() == (0, 0)
+    rid = srv.submit(ctx, w["pos"][:5], 3, 0.3, 0.5, seed=1)  # a smaller request fits
+    e, n, _ = run_until_done(srv, [rid])[rid]
+    assert np.all(np.isfinite(e))
+
+
+def test_cancel_queued_and_active_requests(mods):
+    """Host-side cancellation: an active and a queued request are cancelled;
+    the others finish with the results they have alone, the cancelled ones
+    are reported once and answer EWALD_ERR_CANCELLED."""
+    ewald, serve = mods
+    w = I.workload("heg3d_sc_n54", 6)
+    ctx = ewald.context_for(w, precision="mixed")
+    alone = serve.Server("mixed", max_walkers=64)
+    ra = alone.submit(ctx, w["pos"][:4], 20, 0.3, 0.5, seed=77)
+    ref = run_until_done(alone, [ra])[ra]
+    srv = serve.Server("mixed", max_walkers=10)
+    keep = srv.submit(ctx, w["pos"][:4], 20, 0.3, 0.5, seed=77)
+    active = srv.submit(ctx, w["pos"], 50, 0.3, 0.5, seed=5)   # 4 + 6 walkers: both admitted
+    queued = srv.submit(ctx, w["pos"], 50, 0.3, 0.5, seed=6)   # waits for slots
+    for _ in range(3):
+        a, q = srv.step()
+    assert (a, q) == (2, 1)
+    srv.cancel(active)
+    srv.cancel(queued)
+    with pytest.raises(ewald.EwaldError) as ei:
+        srv.cancel(queued)
+    assert ei.value.code == 8                                # already cancelled
+    done, out = [], None
+    for _ in range(200):
+        srv.step()
+        done += srv.completed()
+        r = srv.result(keep)
+        if r is not None:
+            out = r
+        if out is not None and len(done) == 3:
+            break
+    assert sorted(done) == sorted([keep, active, queued])
+    assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+    for rid in (active, queued):
+        with pytest.raises(ewald.EwaldError) as ei:
+            srv.result(rid)
+        assert ei.value.code == 9
+    with pytest.raises(ewald.EwaldError) as ei:
+        srv.cancel(keep)                                     # finished
+    assert ei.value.code == 8
+    srv.step()
+    assert srv.completed() == []

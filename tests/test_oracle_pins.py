@@ -158,6 +158,26 @@ def test_delta_e_against_two_energies(dim):
         assert abs(de) > 1e-6
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_delta_e_parts_against_two_energies(dim):
+    """The real-space and reciprocal parts of a move each equal the change of
+    that piece between two full energies (the other pieces do not move)."""
+    lat, pos, q, alpha = _random_system(dim, 8)
+    rc, gc = oracle.cutoffs(dim, alpha)
+    _, c0 = oracle.energy(dim, lat, pos, q, alpha, rc, gc)
+    rng = np.random.default_rng(19)
+    for k in (1, 6):
+        r_new = pos[k] + rng.normal(size=dim) * 0.7
+        d_real, d_recip = oracle.delta_e_parts(dim, lat, pos, q, k, r_new, alpha, rc, gc)
+        moved = pos.copy()
+        moved[k] = r_new
+        _, c1 = oracle.energy(dim, lat, moved, q, alpha, rc, gc)
+        assert abs(d_real - (c1[0] - c0[0])) < 1e-11 * scale(c0)
+        assert abs(d_recip - (c1[2] - c0[2])) < 1e-11 * scale(c0)
+        assert np.array_equal(c1[[1, 3, 4]], c0[[1, 3, 4]])
+        assert abs(d_real + d_recip - oracle.delta_e(dim, lat, pos, q, k, r_new, alpha, rc, gc)) < 1e-14 * scale(c0)
+
+
 # ---------------------------------------------------------------- P6
 
 @pytest.mark.parametrize("dim,n", [(3, 2), (3, 4), (2, 3)])
@@ -167,6 +187,22 @@ def test_rho_against_pair_double_sum(dim, n):
     _, comp = oracle.energy(dim, lat, pos, q, alpha, rc, gc)
     e_pairs = oracle.recip_pairsum(dim, lat, pos, q, alpha, gc)
     assert abs(comp[2] - e_pairs) < 1e-12 * abs(e_pairs)
+
+
+def test_rho_at_phase_sign_one_particle():
+    """rho(G) = q e^{+iG.r} for one particle: the sign of the phase, which
+    conjugate symmetry, the origin value and periodicity leave open."""
+    lat = np.array([[5.0, 0.0, 0.0], [1.0, 4.0, 0.0], [0.5, -0.7, 6.0]])
+    r = np.array([[0.9, 1.3, -0.4]])
+    nv = np.array([[1, 0, 0], [0, 2, -1], [3, -1, 2]])
+    B = 2 * np.pi * np.linalg.inv(lat).T                 # rows b_k, a_i . b_k = 2 pi delta_ik
+    rho = oracle.rho_at(3, lat, r, np.array([2.5]), nv)
+    for g, n in enumerate(nv):
+        ph = (n @ B) @ r[0]
+        assert abs(rho[g] - 2.5 * complex(math.cos(ph), math.sin(ph))) < 1e-13
+    # a quarter period along a_1 turns rho(b_1) by +i
+    rq = oracle.rho_at(3, lat, 0.25 * lat[:1], np.array([1.0]), nv[:1])[0]
+    assert abs(rq - 1j) < 1e-14
 
 
 def test_rho_at_conjugate_symmetry_and_origin():

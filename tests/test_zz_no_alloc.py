@@ -14,7 +14,7 @@ from paper_2507_02888_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-6}
+TOL = {"fp64": 1e-12, "mixed": 1e-6, "fp64_tiered": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +38,7 @@ def hex_case(W):
                 fixed_q=np.zeros(0))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
 @pytest.mark.parametrize("case", ["sc54", "hex70", "diamond"])
 def test_noalloc_matches_energy_twice(env, case, prec):
     torch, ewald, lib = env
@@ -68,6 +68,29 @@ def test_noalloc_matches_energy_twice(env, case, prec):
         assert np.all(np.abs(got - ref) <= TOL[prec] * floor), (call, got, ref)
     # the ordinary path is unaffected afterwards
     assert np.allclose(b.energy(), ref, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
+def test_noalloc_matches_oracle(env, prec):
+    """The allocation-free energies against the FP64 CPU oracle directly,
+    element by element, at the context's own cutoffs."""
+    import oracle
+    torch, ewald, lib = env
+    w = I.workload("diamond_3x3x3", 3)
+    ctx = ewald.context_for(w, precision=prec, stream=torch.cuda.current_stream())
+    info = ctx.info()
+    pos_d = torch.tensor(w["pos"], device="cuda")
+    e_d = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    code = lib.ewald_energy_noalloc(ctx._h, pos_d.data_ptr(), 3, e_d.data_ptr(), None)
+    assert code == 0, lib.ewald_last_error_message(ctx._h)
+    torch.cuda.synchronize()
+    got = e_d.cpu().numpy()
+    q = np.concatenate([w["q"], w["fixed_q"]])
+    for i in range(3):
+        p = np.concatenate([w["pos"][i], w["fixed_pos"]])
+        e_o, c = oracle.energy(3, w["lattice"], p, q, w["alpha"], info["r_cutoff"], info["g_cutoff"])
+        floor = max(abs(e_o), 1e-2 * (abs(c[0]) + abs(c[2]) + abs(c[1] + c[3]) + abs(c[4])))
+        assert abs(got[i] - e_o) <= TOL[prec] * floor, (i, got[i], e_o)
 
 
 def test_noalloc_rejects_too_many_walkers(env):
