@@ -27,7 +27,7 @@ from paper_2507_02888_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "mixed": 1e-6, "fp64_tiered": 1e-12}
-DE_TOL = {"fp64": 1e-12, "mixed": 5e-5, "fp64_tiered": 2e-10}
+DE_TOL = {"fp64": 1e-12, "mixed": 3e-4, "fp64_tiered": 2e-10}
 SAMPLE = [0, 2047, 4095]
 
 

