@@ -50,12 +50,23 @@ int apply_tiling(ewald_ctx *c, int S, int bits) {
     cudaError_t e;
     if (bits != t.sub_bits || t.cand.empty()) set_subcells(&t, bits);
     free_one(c->dev, s.cand);
+    free_one(c->dev, s.cand8);
     free_one(c->dev, s.items);
     s.cand = nullptr;
+    s.cand8 = nullptr;
     s.items = nullptr;
     s.sub_bits = t.sub_bits;
     s.cand_max = t.cand_max;
     if ((e = upload(c->dev, (unsigned short **)&s.cand, t.cand.data(), t.cand.size()))) return cuda_fail(c, e);
+    {   // rows padded to a multiple of 8 entries (16-byte loads of 8 indices)
+        const int stride = (t.cand_max + 7) / 8 * 8, n_sub = (int)(t.cand.size() / std::max(t.cand_max, 1));
+        std::vector<unsigned short> c8((size_t)n_sub * stride, (unsigned short)s.n_img);
+        for (int r = 0; r < n_sub; ++r)
+            std::copy(t.cand.begin() + (size_t)r * t.cand_max, t.cand.begin() + (size_t)(r + 1) * t.cand_max,
+                      c8.begin() + (size_t)r * stride);
+        s.cand_stride = stride;
+        if ((e = upload(c->dev, (unsigned short **)&s.cand8, c8.data(), c8.size()))) return cuda_fail(c, e);
+    }
     s.tile = 32 * S;
     s.n_mob_tiles = (t.n_mob + s.tile - 1) / s.tile;
     int nft = (t.n_fix + s.tile - 1) / s.tile;
@@ -88,6 +99,9 @@ int build_device(ewald_ctx *c) {
             s.A32lo[k][x] = (float)(std::ldexp(t.A[k][x], -32) - (double)s.A32[k][x]);
             s.Binv[k][x] = t.Ainv[x][k];
         }
+    s.q_uniform = 1;
+    for (double q : t.q_mob) s.q_uniform &= (float)q == (float)t.q_mob[0];
+    for (double q : t.q_fix) s.q_uniform &= (float)q == (float)t.q_fix[0];
     s.alpha = t.alpha;
     s.alpha_f = (float)t.alpha;
     s.alpha_lo_f = (float)(t.alpha - (double)s.alpha_f);

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "energy_items.cuh"
+#include "real_mixed.cuh"
 
 namespace ewald {
 
@@ -131,8 +132,8 @@ static size_t real_smem(const SysDev &s, int precision) {
     if (s.tier2_f > 0)
         return ImageSmem<float>::bytes(s, s.dim) + align16((s.n_img + 1) * sizeof(float4)) +
                real_work_bytes(s, precision, kRealWarps, true);
-    size_t img = precision == EWALD_FP64 ? ImageSmem<double>::bytes(s, s.dim) : ImageSmem<float>::bytes(s, s.dim);
-    return img + real_work_bytes(s, precision, kRealWarps);
+    if (precision != EWALD_FP64) return MixedImageSmem::bytes(s, s.dim) + mixed_real_work_bytes(s, kRealWarps);
+    return ImageSmem<double>::bytes(s, s.dim) + real_work_bytes(s, precision, kRealWarps);
 }
 
 template <typename F>
@@ -180,13 +181,10 @@ int configure_launch(SysDev &s, int precision, LaunchCfg *cfg) {
     } else {
         if (s.dim == 3) {
             if ((e = allow_smem(k_sfac<float, 3>, cfg->sfac_smem))) return e;
-            if ((e = allow_smem(k_real<float, 3>, cfg->real_smem))) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_real<float, 3>, kRealThreads, cfg->real_smem);
         } else {
             if ((e = allow_smem(k_sfac<float, 2>, cfg->sfac_smem))) return e;
-            if ((e = allow_smem(k_real<float, 2>, cfg->real_smem))) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_real<float, 2>, kRealThreads, cfg->real_smem);
         }
+        e = (cudaError_t)configure_real_mixed(s, cfg->real_smem, &occ);
     }
     if (e) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
@@ -235,8 +233,7 @@ int launch_real(const SysDev &s, const BatchDev &b, int precision, const LaunchC
         if (s.dim == 3) k_real<double, 3><<<grid, kRealThreads, cfg.real_smem, st>>>(s, b);
         else k_real<double, 2><<<grid, kRealThreads, cfg.real_smem, st>>>(s, b);
     } else {
-        if (s.dim == 3) k_real<float, 3><<<grid, kRealThreads, cfg.real_smem, st>>>(s, b);
-        else k_real<float, 2><<<grid, kRealThreads, cfg.real_smem, st>>>(s, b);
+        return launch_real_mixed(s, b, grid, cfg.real_smem, st);
     }
     return cudaGetLastError();
 }

@@ -8,8 +8,11 @@
 // walker's partial sums (in a fixed order, so results do not depend on the
 // schedule or on the other systems in the launch).  No CTA ever waits for
 // another one.
+#include <type_traits>
+
 #include "energy_items.cuh"
 #include "multi.h"
+#include "real_mixed.cuh"
 
 namespace ewald {
 
@@ -38,7 +41,9 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(R) == 4 ? kMultiMinBlock
     __shared__ SysDev ss;
     __shared__ BatchDev sb;
     __shared__ int s_item, s_last, s_img_sys;
-    ImageSmem<R> ims;
+    // candidate tables: the FP64 loop's (ImageSmem) or the mixed loop's
+    using Ims = typename std::conditional<sizeof(R) == 4, MixedImageSmem, ImageSmem<R>>::type;
+    Ims ims;
     unsigned char *work = smem + m.img_bytes;
     if (threadIdx.x == 0) s_img_sys = -1;
     for (;;) {
@@ -64,8 +69,13 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(R) == 4 ? kMultiMinBlock
             else sfac_item<R, 2>(ss, sb, d.z, d.w, ss.sfac_te, true, work);
         } else {
             const int js = multi_jsplit(ss);
-            if (ss.dim == 3) real_item<R, 3>(ss, sb, d.z, d.w, ims, work, js);
-            else real_item<R, 2>(ss, sb, d.z, d.w, ims, work, js);
+            if constexpr (sizeof(R) == 4) {
+                if (ss.dim == 3) real_item_mixed<3>(ss, sb, d.z, d.w, ims, work, js);
+                else real_item_mixed<2>(ss, sb, d.z, d.w, ims, work, js);
+            } else {
+                if (ss.dim == 3) real_item<R, 3>(ss, sb, d.z, d.w, ims, work, js);
+                else real_item<R, 2>(ss, sb, d.z, d.w, ims, work, js);
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -84,10 +94,11 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(R) == 4 ? kMultiMinBlock
 size_t multi_energy_smem(const std::vector<SysDev> &sys, int precision, size_t *img_bytes) {
     size_t img = 0, work = 0;
     for (const SysDev &s : sys) {
-        size_t ib = precision == EWALD_FP64 ? ImageSmem<double>::bytes(s, s.dim) : ImageSmem<float>::bytes(s, s.dim);
+        size_t ib = precision == EWALD_FP64 ? ImageSmem<double>::bytes(s, s.dim) : MixedImageSmem::bytes(s, s.dim);
         img = std::max(img, ib);
         work = std::max(work, sfac_bytes(s, precision, s.sfac_te, kMultiThreads));
-        work = std::max(work, real_work_bytes(s, precision, kMultiThreads / 32));
+        work = std::max(work, precision == EWALD_FP64 ? real_work_bytes(s, precision, kMultiThreads / 32)
+                                                      : mixed_real_work_bytes(s, kMultiThreads / 32));
     }
     *img_bytes = img;
     return img + work;

@@ -1,0 +1,56 @@
+// The mixed path's real-space kernel (pair loop in real_mixed.cuh):
+// persistent CTAs over (walker, tile pair) items, one instantiation per
+// candidate-list length and charge pattern, chosen on the host so that
+// each is compiled with the registers of its own loop.
+#include "real_mixed.cuh"
+
+namespace ewald {
+
+template <int DIM, int CM, bool QW>
+__global__ void __launch_bounds__(kRealThreads, kRealMinBlocksMixed) k_real_mixed(SysDev s, BatchDev b) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    MixedImageSmem ims;
+    ims.carve(smem, s, DIM);
+    ims.stage(s, DIM);
+    unsigned char *work = smem + MixedImageSmem::bytes(s, DIM);
+    const long long total = (long long)b.W * s.n_items;
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        const int w = (int)(item / s.n_items), p = (int)(item - (long long)w * s.n_items);
+        real_item_mixed_cm<DIM, CM, QW>(s, b, w, p, ims, work, 1);
+    }
+}
+
+using RealFn = void (*)(SysDev, BatchDev);
+
+template <int DIM, bool QW>
+static RealFn pick_cm(int cm) {
+    switch (cm) {
+        case 1: return k_real_mixed<DIM, 1, QW>;
+        case 2: return k_real_mixed<DIM, 2, QW>;
+        case 3: return k_real_mixed<DIM, 3, QW>;
+        case 4: return k_real_mixed<DIM, 4, QW>;
+        case 6: return k_real_mixed<DIM, 6, QW>;
+        case 8: return k_real_mixed<DIM, 8, QW>;
+        default: return k_real_mixed<DIM, 0, QW>;
+    }
+}
+
+static RealFn real_mixed_fn(const SysDev &s) {
+    const int cm = mixed_cm(s.cand_max);
+    if (s.dim == 3) return s.q_uniform ? pick_cm<3, false>(cm) : pick_cm<3, true>(cm);
+    return s.q_uniform ? pick_cm<2, false>(cm) : pick_cm<2, true>(cm);
+}
+
+int configure_real_mixed(const SysDev &s, size_t smem, int *blocks_per_sm) {
+    const RealFn f = real_mixed_fn(s);
+    cudaError_t e = allow_max_smem(f, smem);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kRealThreads, smem);
+    return e;
+}
+
+int launch_real_mixed(const SysDev &s, const BatchDev &b, int grid, size_t smem, cudaStream_t st) {
+    real_mixed_fn(s)<<<grid, kRealThreads, smem, st>>>(s, b);
+    return cudaGetLastError();
+}
+
+}  // namespace ewald
