@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "capi_internal.h"
+#include "real_mixed.cuh"
 #include "move_tiered.h"
 #include "multi.h"
 #include "sfac_df.h"
@@ -50,22 +51,47 @@ int apply_tiling(ewald_ctx *c, int S, int bits) {
     cudaError_t e;
     if (bits != t.sub_bits || t.cand.empty()) set_subcells(&t, bits);
     free_one(c->dev, s.cand);
-    free_one(c->dev, s.cand8);
+    free_one(c->dev, s.cxy);
+    free_one(c->dev, s.cz);
+    free_one(c->dev, s.clist);
     free_one(c->dev, s.items);
     s.cand = nullptr;
-    s.cand8 = nullptr;
+    s.cxy = nullptr;
+    s.cz = nullptr;
+    s.clist = nullptr;
     s.items = nullptr;
     s.sub_bits = t.sub_bits;
     s.cand_max = t.cand_max;
     if ((e = upload(c->dev, (unsigned short **)&s.cand, t.cand.data(), t.cand.size()))) return cuda_fail(c, e);
-    {   // rows padded to a multiple of 8 entries (16-byte loads of 8 indices)
-        const int stride = (t.cand_max + 7) / 8 * 8, n_sub = (int)(t.cand.size() / std::max(t.cand_max, 1));
-        std::vector<unsigned short> c8((size_t)n_sub * stride, (unsigned short)s.n_img);
-        for (int r = 0; r < n_sub; ++r)
-            std::copy(t.cand.begin() + (size_t)r * t.cand_max, t.cand.begin() + (size_t)(r + 1) * t.cand_max,
-                      c8.begin() + (size_t)r * stride);
-        s.cand_stride = stride;
-        if ((e = upload(c->dev, (unsigned short **)&s.cand8, c8.data(), c8.size()))) return cuda_fail(c, e);
+    {   // the mixed loop's tables: distinct lists as pairs of FP32 images
+        const int np = mixed_pairs(t.cand_max), n_sub = (int)(t.cand.size() / std::max(t.cand_max, 1));
+        std::map<std::vector<unsigned short>, int> ids;
+        std::vector<unsigned short> clist(n_sub);
+        std::vector<float4> cxy;
+        std::vector<float2> cz;
+        auto imf = [&](int i, int y) {  // FP32 image component, as in the FP32 image table
+            return i < s.n_img ? (float)t.img[3 * i + y] : 1e18f;
+        };
+        for (int r = 0; r < n_sub; ++r) {
+            std::vector<unsigned short> l(2 * np, (unsigned short)s.n_img);
+            std::copy(t.cand.begin() + (size_t)r * t.cand_max, t.cand.begin() + (size_t)(r + 1) * t.cand_max, l.begin());
+            auto it = ids.find(l);
+            if (it == ids.end()) {
+                it = ids.emplace(l, (int)ids.size()).first;
+                for (int p = 0; p < np; ++p) {
+                    const int a = l[2 * p], b = l[2 * p + 1];
+                    cxy.push_back(make_float4(imf(a, 0), imf(b, 0), imf(a, 1), imf(b, 1)));
+                    cz.push_back(make_float2(t.dim == 3 ? imf(a, 2) : 0.0f, t.dim == 3 ? imf(b, 2) : 0.0f));
+                }
+            }
+            clist[r] = (unsigned short)it->second;
+        }
+        if (ids.size() > 65535) return fail(c, EWALD_ERR_ARG, "too many distinct candidate lists");
+        s.n_lists = (int)ids.size();
+        s.cand_pairs = np;
+        if ((e = upload(c->dev, (float4 **)&s.cxy, cxy.data(), cxy.size()))) return cuda_fail(c, e);
+        if ((e = upload(c->dev, (float2 **)&s.cz, cz.data(), cz.size()))) return cuda_fail(c, e);
+        if ((e = upload(c->dev, (unsigned short **)&s.clist, clist.data(), clist.size()))) return cuda_fail(c, e);
     }
     s.tile = 32 * S;
     s.n_mob_tiles = (t.n_mob + s.tile - 1) / s.tile;

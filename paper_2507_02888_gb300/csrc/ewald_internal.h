@@ -29,8 +29,9 @@ constexpr int kRealWarps = 4;          // warps per real-space CTA
 constexpr int kRealThreads = 32 * kRealWarps;
 // resident real-space CTAs per SM the registers are sized for (FP32, FP64 path)
 constexpr int kRealMinBlocks32 = 11, kRealMinBlocks64 = 8;
-// resident CTAs per SM the registers of the mixed path's pair loop are sized for
-constexpr int kRealMinBlocksMixed = 8;
+// the mixed path's real-space kernel: warps per CTA (sharing one copy of the
+// candidate tables) and resident CTAs per SM its registers are sized for
+constexpr int kRealMixedWarps = 8, kRealMixedThreads = 32 * kRealMixedWarps, kRealMinBlocksMixed = 4;
 // per-warp queues of accepted (r^2, weight) terms: the FP32 one a ring
 // flushed 64 entries at a time, the FP64 one flushed 32 at a time
 constexpr int kQueueCap32 = 128, kQueueCap64 = 96;
@@ -77,10 +78,13 @@ struct SysDev {
     const float4 *img_f;
     const float4 *img_lo_f;  // img_d - img_f: the rounding of the FP32 images (tiered path)
     const unsigned short *cand;
-    // the same lists for the mixed path's pair loop: rows of cand_stride
-    // entries (cand_max rounded up to a multiple of 8, padded with the sentinel)
-    const unsigned short *cand8;
-    int cand_stride;
+    // the same lists for the mixed path's pair loop: each distinct list once,
+    // as cand_pairs pairs of FP32 images (X_a, X_b, Y_a, Y_b) and (Z_a, Z_b),
+    // padded with the sentinel; clist[cell] = the cell's list
+    const float4 *cxy;
+    const float2 *cz;
+    const unsigned short *clist;
+    int n_lists, cand_pairs;
     int q_uniform;  // every mobile charge equal and every fixed charge equal
     int tile, n_mob_tiles, n_items;  // pair tiles (T = tile) and items per walker
     const int2 *items;               // (ti, tj); tj >= n_mob_tiles -> fixed tile tj - n_mob_tiles

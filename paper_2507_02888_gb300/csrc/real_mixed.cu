@@ -7,7 +7,7 @@
 namespace ewald {
 
 template <int DIM, int CM, bool QW>
-__global__ void __launch_bounds__(kRealThreads, kRealMinBlocksMixed) k_real_mixed(SysDev s, BatchDev b) {
+__global__ void __launch_bounds__(kRealMixedThreads, kRealMinBlocksMixed) k_real_mixed(SysDev s, BatchDev b) {
     extern __shared__ __align__(32) unsigned char smem[];
     MixedImageSmem ims;
     ims.carve(smem, s, DIM);
@@ -16,7 +16,8 @@ __global__ void __launch_bounds__(kRealThreads, kRealMinBlocksMixed) k_real_mixe
     const long long total = (long long)b.W * s.n_items;
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int w = (int)(item / s.n_items), p = (int)(item - (long long)w * s.n_items);
-        real_item_mixed_cm<DIM, CM, QW>(s, b, w, p, ims, work, 1);
+        // units of 32 x 16 pairs: at least as many as the CTA has warps
+        real_item_mixed_cm<DIM, CM, QW>(s, b, w, p, ims, work, 2);
     }
 }
 
@@ -25,9 +26,7 @@ using RealFn = void (*)(SysDev, BatchDev);
 template <int DIM, bool QW>
 static RealFn pick_cm(int cm) {
     switch (cm) {
-        case 1: return k_real_mixed<DIM, 1, QW>;
         case 2: return k_real_mixed<DIM, 2, QW>;
-        case 3: return k_real_mixed<DIM, 3, QW>;
         case 4: return k_real_mixed<DIM, 4, QW>;
         case 6: return k_real_mixed<DIM, 6, QW>;
         case 8: return k_real_mixed<DIM, 8, QW>;
@@ -44,12 +43,12 @@ static RealFn real_mixed_fn(const SysDev &s) {
 int configure_real_mixed(const SysDev &s, size_t smem, int *blocks_per_sm) {
     const RealFn f = real_mixed_fn(s);
     cudaError_t e = allow_max_smem(f, smem);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kRealThreads, smem);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kRealMixedThreads, smem);
     return e;
 }
 
 int launch_real_mixed(const SysDev &s, const BatchDev &b, int grid, size_t smem, cudaStream_t st) {
-    real_mixed_fn(s)<<<grid, kRealThreads, smem, st>>>(s, b);
+    real_mixed_fn(s)<<<grid, kRealMixedThreads, smem, st>>>(s, b);
     return cudaGetLastError();
 }
 

@@ -6,7 +6,9 @@
 // the sub-tile (staged in shared memory, read as a broadcast).  For one pair
 // a lane forms the exact fixed-point difference, its displacement cell and
 // its Cartesian vector, then tests the cell's candidate images, a list of
-// compile-time length CM (16-bit image indices, eight to a 16-byte load).
+// compile-time length CM stored as pairs of images in the operand layout of
+// the paired FP32 instructions (one 16-byte and one 8-byte load and six
+// paired operations per two images).
 // Images inside r_c are not compacted across the warp: every lane appends
 // the r^2 of its passing images to a ring of its own in shared
 // memory (column `lane` of a [kLaneRing][32] array: no bank conflicts, no
@@ -34,31 +36,38 @@ constexpr int kLaneRing = 32;  // pending terms per lane (a power of two)
 // A particle of the FP32 pair loop in shared memory: the top 32 bits of the
 // fixed-point coordinates and the charge; in a 2D cell the third word holds
 // the height (float bits) of a layered cell, 0 otherwise.
-struct Tile16 {
+struct __align__(16) Tile16 {
     unsigned u[3];
     float q;
 };
 
-// Candidate tables of the FP32 pair loop in shared memory: the FP32 image
-// table and, per displacement cell, the indices of its candidates
-// (cand_stride entries, a multiple of 8, padded with the far sentinel).
+// Candidate tables of the FP32 pair loop in shared memory.  The candidate
+// lists of the displacement cells are stored once per distinct list (many
+// cells share a list), as pairs of images in the operand layout of the
+// paired FP32 instructions: for pair p of list L, xy[L][p] = (X_a, X_b,
+// Y_a, Y_b) and, in 3D, z[L][p] = (Z_a, Z_b) (lists padded with the far
+// sentinel to cand_pairs pairs); clist[cell] is the cell's list.
 struct MixedImageSmem {
-    float4 *img;
-    unsigned short *coff;
+    float4 *xy;
+    float2 *z;
+    unsigned short *clist;
     __host__ __device__ static size_t bytes(const SysDev &s, int dim) {
-        const size_t n_sub = (size_t)1 << (s.sub_bits * dim);
-        return align16((s.n_img + 1) * sizeof(float4)) + align16(n_sub * s.cand_stride * sizeof(unsigned short));
+        const size_t n_sub = (size_t)1 << (s.sub_bits * dim), np = (size_t)s.n_lists * s.cand_pairs;
+        return align16(np * sizeof(float4)) + (dim == 3 ? align16(np * sizeof(float2)) : 0) +
+               align16(n_sub * sizeof(unsigned short));
     }
     __device__ void carve(unsigned char *base, const SysDev &s, int dim) {
-        img = (float4 *)base;
-        coff = (unsigned short *)(base + align16((s.n_img + 1) * sizeof(float4)));
+        const size_t np = (size_t)s.n_lists * s.cand_pairs;
+        xy = (float4 *)base;
+        z = (float2 *)(base + align16(np * sizeof(float4)));
+        clist = (unsigned short *)(base + align16(np * sizeof(float4)) + (dim == 3 ? align16(np * sizeof(float2)) : 0));
     }
     __device__ void stage(const SysDev &s, int dim) {
-        const int n_sub = 1 << (s.sub_bits * dim);
-        for (int i = threadIdx.x; i <= s.n_img; i += blockDim.x) img[i] = s.img_f[i];
-        const uint4 *src = (const uint4 *)s.cand8;
-        uint4 *dst = (uint4 *)coff;
-        for (int i = threadIdx.x; i < n_sub * s.cand_stride / 8; i += blockDim.x) dst[i] = src[i];
+        const int n_sub = 1 << (s.sub_bits * dim), np = s.n_lists * s.cand_pairs;
+        for (int i = threadIdx.x; i < np; i += blockDim.x) xy[i] = s.cxy[i];
+        if (dim == 3)
+            for (int i = threadIdx.x; i < np; i += blockDim.x) z[i] = s.cz[i];
+        for (int i = threadIdx.x; i < n_sub; i += blockDim.x) clist[i] = s.clist[i];
     }
 };
 
@@ -213,46 +222,55 @@ __device__ __forceinline__ int pair_cart(const SysDev &s, const Tile16 &a, const
     return sc;
 }
 
-// Candidate c (compile-time) of a list chunk whose eight indices are L
-template <int C>
-__device__ __forceinline__ unsigned cand_index(const uint4 &L) {
-    const unsigned wd = (C >> 1) == 0 ? L.x : (C >> 1) == 1 ? L.y : (C >> 1) == 2 ? L.z : L.w;
-    return (C & 1) ? (wd >> 16) : (wd & 0xffffu);
+__device__ __forceinline__ float4 lds128(const float4 *p) {
+    float4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
 }
 
-// Test NC (compile-time) candidates of one list chunk and push the passing
-// r^2; FIRST: the chunk holds candidate 0, the only image through which a
-// displacement of the cell can come within the close radius: a close pair
-// is recorded for FP64 instead.
-template <int DIM, int NC, bool FIRST, bool QW>
-__device__ __forceinline__ void test_chunk(const float4 *img, const uint4 &L, const float *x, float z2,
-                                           float rc2, float close2, float wgt, LaneRing<QW> &ring, bool &close) {
+// Test NP (compile-time) candidate pairs of a list, two images per paired
+// instruction (each component rounded as image_r2 rounds it), and push the
+// r^2 that pass; FIRST: the pairs start with candidate 0, the only image
+// through which a displacement of the cell can come within the close
+// radius: a close pair is recorded for FP64 instead.
+template <int DIM, int NP, bool FIRST, bool QW>
+__device__ __forceinline__ void test_pairs(const float4 *xy, const float2 *zz, const float *x, float z2, float rc2,
+                                           float close2, float wgt, LaneRing<QW> &ring, bool &close) {
+    const float2 x0 = splat(x[0]), x1 = splat(x[1]), zs = splat(z2);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        unsigned ix;
-        switch (c) {
-            case 0: ix = cand_index<0>(L); break;
-            case 1: ix = cand_index<1>(L); break;
-            case 2: ix = cand_index<2>(L); break;
-            case 3: ix = cand_index<3>(L); break;
-            case 4: ix = cand_index<4>(L); break;
-            case 5: ix = cand_index<5>(L); break;
-            case 6: ix = cand_index<6>(L); break;
-            default: ix = cand_index<7>(L); break;
+    for (int p = 0; p < NP; ++p) {
+        const float4 XY = lds128(xy + p);
+        const float2 y0 = add2(x0, make_float2(XY.x, XY.y)), y1 = add2(x1, make_float2(XY.z, XY.w));
+        float2 r2 = fma2(y1, y1, fma2(y0, y0, zs));
+        if (DIM == 3) {
+            const float2 y2 = add2(splat(x[DIM - 1]), zz[p]);
+            r2 = fma2(y2, y2, r2);
         }
-        const float4 R = img[ix];
-        const float r2 = image_r2<DIM>(x, R, z2);
-        bool pass = r2 < rc2;
-        if (FIRST && c == 0) {
-            close = pass && r2 < close2;
-            pass = pass && !close;
+        bool pa = r2.x < rc2;
+        const bool pb = r2.y < rc2;
+        if (FIRST && p == 0) {
+            close = pa && r2.x < close2;
+            pa = pa && !close;
         }
-        ring.push(pass, r2, wgt);
+        ring.push(pa, r2.x, wgt);
+        ring.push(pb, r2.y, wgt);
     }
 }
 
-// The images of one pair: CM candidates (CM <= 8 compile-time; CM = 0: the
-// list in chunks of 8, padded with the sentinel)
+// Candidate slots with a compiled pair loop (pairs of images); a list of
+// another length runs the next longer one (padded with the sentinel),
+// longer than 8 the chunked loop (slots = 0: chunks of 4 pairs).
+__host__ __device__ inline int mixed_cm(int cand_max) {
+    return cand_max <= 2 ? 2 : cand_max <= 4 ? 4 : cand_max <= 6 ? 6 : cand_max <= 8 ? 8 : 0;
+}
+__host__ __device__ inline int mixed_pairs(int cand_max) {
+    const int cm = mixed_cm(cand_max);
+    return cm ? cm / 2 : (cand_max + 7) / 8 * 4;
+}
+
+// The images of one pair of particles: CM candidate slots (CM = 2 ... 8
+// compile-time; CM = 0: the list in chunks of 4 pairs)
 template <int DIM, int CM, bool QW>
 __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem &ims, const Tile16 &a,
                                           const Tile16 &b, bool valid, float wgt, LaneRing<QW> &ring, bool &close,
@@ -260,17 +278,18 @@ __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem 
     float x[DIM], z2;
     const int sc = pair_cart<DIM>(s, a, b, x, z2);
     const float rc2 = valid ? s.rc2_f : 0.0f;  // invalid lanes never pass
-    const float4 *img = ims.img;
-    const uint4 *lst = (const uint4 *)(ims.coff + sc * s.cand_stride);
+    const int base = ims.clist[sc] * s.cand_pairs;
+    const float4 *xy = ims.xy + base;
+    const float2 *zz = ims.z + base;
     if (CM > 0) {
-        test_chunk<DIM, CM, true, QW>(img, lst[0], x, z2, rc2, s.close2_f, wgt, ring, close);
+        test_pairs<DIM, CM / 2, true, QW>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
         ring.template service<CM>(acc, tk);
     } else {
-        test_chunk<DIM, 8, true, QW>(img, lst[0], x, z2, rc2, s.close2_f, wgt, ring, close);
+        test_pairs<DIM, 4, true, QW>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
         ring.template service<8>(acc, tk);
-        for (int ch = 1; ch < s.cand_stride / 8; ++ch) {
+        for (int ch = 4; ch < s.cand_pairs; ch += 4) {
             bool unused;
-            test_chunk<DIM, 8, false, QW>(img, lst[ch], x, z2, rc2, s.close2_f, wgt, ring, unused);
+            test_pairs<DIM, 4, false, QW>(xy + ch, zz + ch, x, z2, rc2, s.close2_f, wgt, ring, unused);
             ring.template service<8>(acc, tk);
         }
     }
@@ -361,7 +380,7 @@ __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, in
                     const int gli = (int)(id >> 16), glj = (int)(id & 0xffffu);
                     float x[DIM], z2;
                     const int sc = pair_cart<DIM>(s, ti[gli], tj[glj], x, z2);
-                    const int c0 = ims.coff[sc * s.cand_stride];
+                    const int c0 = s.cand[sc * s.cand_max];
                     acc64 += close_term_global<DIM>(s, b, w, i0 + gli, j0 + glj, fixedj, c0,
                                                     (double)ti[gli].q * (double)tj[glj].q);
                 }
@@ -372,8 +391,8 @@ __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, in
                     const Tile16 pj = tj[lj];
                     float x[DIM], z2;
                     const int sc = pair_cart<DIM>(s, pi, pj, x, z2);
-                    const int c0 = ims.coff[sc * s.cand_stride];
-                    const float r2 = image_r2<DIM>(x, ims.img[c0], z2);
+                    const int c0 = s.cand[sc * s.cand_max];
+                    const float r2 = image_r2<DIM>(x, s.img_f[c0], z2);
                     const bool valid = vi && (!self || lane < jj);
                     if (valid && r2 < s.rc2_f && r2 < s.close2_f)
                         acc64 += close_term_global<DIM>(s, b, w, i0 + li, j0 + lj, fixedj, c0,
@@ -394,13 +413,6 @@ __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, in
     }
 }
 
-// Candidate-list lengths with a compiled pair loop; a list of another
-// length runs the next longer one (padded with the sentinel), longer than 8
-// the chunked loop (CM = 0).
-__host__ __device__ inline int mixed_cm(int cand_max) {
-    return cand_max <= 4 ? cand_max : cand_max <= 6 ? 6 : cand_max <= 8 ? 8 : 0;
-}
-
 // Dispatch on the candidate-list length and the charge pattern of the
 // system (for kernels that take items of several systems)
 template <int DIM>
@@ -411,9 +423,7 @@ __device__ void real_item_mixed(const SysDev &s, const BatchDev &b, int w, int p
     else real_item_mixed_cm<DIM, CM, true>(s, b, w, p, ims, work, jsplit);                  \
     break;
     switch (mixed_cm(s.cand_max)) {
-        case 1: EWALD_RIM(1)
         case 2: EWALD_RIM(2)
-        case 3: EWALD_RIM(3)
         case 4: EWALD_RIM(4)
         case 6: EWALD_RIM(6)
         case 8: EWALD_RIM(8)
