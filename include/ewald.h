@@ -103,7 +103,7 @@ typedef struct {
     int n_g_half;         /* G vectors kept, one of each +-G pair */
     int n_images;         /* distinct lattice vectors that may meet the real-space cutoff */
     int subcell_bits;     /* real-space displacement cells: 2^bits per axis */
-    int pair_tile;        /* particles per side of a real-space pair tile (32, 64, 128) */
+    int pair_tile;        /* particles per side of a real-space pair tile (32, 64, 128; 256 in the mixed form) */
     int max_candidates;   /* longest candidate-image list of a displacement cell */
     int n_runs, run_len;  /* G rows split into runs of <= run_len consecutive n1 */
     double e_madelung;    /* 1/2 sum q^2 sum_{R!=0} erfc(alpha R)/R  (all charges) */
@@ -266,7 +266,8 @@ const char *ewald_server_error_message(const ewald_server *srv);
 
 /* Autotuner.  Times the real-space kernel on (up to 512 of) the batch's
  * walkers for every allowed real-space tiling - pair tiles of 32, 64 or 128
- * particles per side x 2^bits displacement cells per axis (candidate lists
+ * particles per side (also 256 in the mixed form) x 2^bits displacement
+ * cells per axis (candidate lists
  * <= 48 KB) - and keeps the fastest in the batch's context.  With
  * cache_path (may be NULL) the result is looked up first and stored after
  * tuning in a small JSON file keyed by the system's shape and the GPU name;

@@ -251,6 +251,9 @@ int build_device(ewald_ctx *c) {
     // pair tiles of 32 x S particles per side; the largest item count (S = 1)
     // sizes the batches' partial-sum buffers, so any tiling fits later
     int S = t.n_mob >= 128 ? 4 : (t.n_mob >= 64 ? 2 : 1);
+    // the mixed form's pair loop takes 256-particle tiles (8 warps, no limit
+    // on the units of an item): a quarter of the item boundaries
+    if (t.precision == EWALD_MIXED && t.n_mob >= 256) S = 8;
     {
         int nt1 = (t.n_mob + 31) / 32, nf1 = (t.n_fix + 31) / 32;
         c->max_items = nt1 * (nt1 + 1) / 2 + nt1 * nf1;
@@ -438,7 +441,7 @@ std::map<std::string, TuneEntry> read_tune_cache(const char *path) {
         if ((p = line.find("\"tile\": ", b)) != std::string::npos) e.tile = std::atoi(line.c_str() + p + 8);
         if ((p = line.find("\"bits\": ", b)) != std::string::npos) e.bits = std::atoi(line.c_str() + p + 8);
         if ((p = line.find("\"ms\": ", b)) != std::string::npos) e.ms = std::atof(line.c_str() + p + 6);
-        if (e.tile == 32 || e.tile == 64 || e.tile == 128) m[line.substr(a, b - a)] = e;
+        if (e.tile == 32 || e.tile == 64 || e.tile == 128 || e.tile == 256) m[line.substr(a, b - a)] = e;
     }
     return m;
 }
@@ -460,6 +463,9 @@ bool write_tune_cache(const char *path, const std::map<std::string, TuneEntry> &
 bool tiling_allowed(const ewald_ctx *c, int S, int bits) {
     const HostTables &t = c->t;
     if (32 * S > std::max(32, 2 * t.n_mob)) return false;
+    // 256-particle tiles: the mixed form's pair loop only (the FP64 and tiered
+    // loops sum at most 16 sub-tile units per item)
+    if (S > 4 && (t.precision != EWALD_MIXED || S != 8)) return false;
     int max_bits = t.dim == 3 ? 4 : 6;
     return bits >= t.min_bits && bits <= max_bits && subcell_bytes(t, bits) <= 48 * 1024;
 }
@@ -1045,7 +1051,7 @@ int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *re
     cudaEventCreate(&e1);
     double best = 1e300;
     int bestS = c->s.tile / 32, bestBits = c->s.sub_bits;
-    const int Ss[3] = {1, 2, 4};
+    const int Ss[4] = {1, 2, 4, 8};
     for (int S : Ss)
         for (int bits = 0; bits <= (c->t.dim == 3 ? 4 : 6); ++bits) {
             if (!tiling_allowed(c, S, bits)) continue;

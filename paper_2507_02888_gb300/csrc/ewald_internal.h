@@ -31,7 +31,7 @@ constexpr int kRealThreads = 32 * kRealWarps;
 constexpr int kRealMinBlocks32 = 11, kRealMinBlocks64 = 8;
 // the mixed path's real-space kernel: warps per CTA (sharing one copy of the
 // candidate tables) and resident CTAs per SM its registers are sized for
-constexpr int kRealMixedWarps = 8, kRealMixedThreads = 32 * kRealMixedWarps, kRealMinBlocksMixed = 4;
+constexpr int kRealMixedWarps = 16, kRealMixedThreads = 32 * kRealMixedWarps, kRealMinBlocksMixed = 2;
 // per-warp queues of accepted (r^2, weight) terms: the FP32 one a ring
 // flushed 64 entries at a time, the FP64 one flushed 32 at a time
 constexpr int kQueueCap32 = 128, kQueueCap64 = 96;

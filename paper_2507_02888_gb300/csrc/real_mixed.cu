@@ -16,8 +16,9 @@ __global__ void __launch_bounds__(kRealMixedThreads, kRealMinBlocksMixed) k_real
     const long long total = (long long)b.W * s.n_items;
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int w = (int)(item / s.n_items), p = (int)(item - (long long)w * s.n_items);
-        // units of 32 x 16 pairs: at least as many as the CTA has warps
-        real_item_mixed_cm<DIM, CM, QW>(s, b, w, p, ims, work, 2);
+        // units of 32 x 8 pairs: a 256 x 256 item splits evenly over the
+        // CTA's 16 warps (diagonal items: 144 units, the others 256)
+        real_item_mixed_cm<DIM, CM, QW>(s, b, w, p, ims, work, 4);
     }
 }
 

@@ -352,6 +352,7 @@ __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, in
             a = st / S;
             c = st - a * S;
         }
+        if (i0 + a * 32 >= s.n_mob) continue;  // a ragged last tile: no particle i in this sub-tile
         const int li = a * 32 + lane;
         const Tile16 pi = ti[li];
         const bool vi = i0 + li < s.n_mob;
