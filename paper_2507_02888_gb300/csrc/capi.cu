@@ -622,6 +622,7 @@ int ewald_batch_create(ewald_ctx *c, int W, ewald_batch **out) {
     chk(dalloc(o, &d.pend_u, (size_t)W * 3));
     chk(dalloc(o, &d.acc_count, W));
     chk(dalloc(o, &d.resum_flag, W));
+    chk(dalloc(o, &d.resum_list, (size_t)W + 1));
     chk(dalloc(o, &d.part_real, (size_t)W * std::max(c->max_items, s.n_items)));
     chk(dalloc(o, &d.part_recip, (size_t)W * s.n_gchunks));
     chk(dalloc(o, &d.e, W));
@@ -768,7 +769,11 @@ int ewald_accept_move(ewald_batch *b, const unsigned char *accept, int on_device
     const int p = c->t.precision;
     int e = timed(c, KT_ACCEPT, [&] { return launch_accept(c->s, b->b, p, c->cfg, da, c->t.resum_every, c->stream); });
     // rebuild rho(G) of the walkers that reached resum_every accepted moves
-    if (!e) e = timed(c, KT_RESUM, [&] { return run_sfac(c, b->b, p, b->b.resum_flag); });
+    // (the mixed accept lists them; the other forms flag them)
+    if (!e) e = timed(c, KT_RESUM, [&] {
+        return p == EWALD_MIXED ? launch_sfac_listed(c->s, b->b, p, c->cfg, c->stream)
+                                : run_sfac(c, b->b, p, b->b.resum_flag);
+    });
     if (e) return cuda_fail(c, (cudaError_t)e);
     b->has_pending = false;
     if (!on_device) return sync_status(b);

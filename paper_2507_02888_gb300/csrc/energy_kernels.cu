@@ -74,6 +74,21 @@ __global__ void __launch_bounds__(kSfacThreads, sizeof(R) == 4 ? kSfacMinBlocks3
     sfac_item<R, DIM>(s, b, w, chunk, te, write_energy != 0, smem);
 }
 
+// The structure factor of the walkers listed in b.resum_list (a count,
+// then walker indices), rho only: persistent CTAs over (listed walker,
+// chunk) items, so that a re-sum after accepted moves costs in proportion
+// to the walkers due, not to the batch.
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kSfacThreads, sizeof(R) == 4 ? kSfacMinBlocks32 : kSfacMinBlocks64)
+    k_sfac_listed(SysDev s, BatchDev b, int te) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    const int n = b.resum_list[0] * s.n_gchunks;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
+        const int w = b.resum_list[1 + it / s.n_gchunks], chunk = it % s.n_gchunks;
+        sfac_item<R, DIM>(s, b, w, chunk, te, false, smem);
+    }
+}
+
 // -------------------------------------------------------------- real space
 // Persistent CTAs walk the (walker, tile pair) items; see real_item.
 template <typename R, int DIM>
@@ -157,6 +172,20 @@ int configure_launch(SysDev &s, int precision, LaunchCfg *cfg) {
     s.sfac_te = te;
     cfg->sfac_smem = sfac_smem(s, precision, te);
     cfg->real_smem = real_smem(s, precision);
+    {   // the listed structure factor: persistent CTAs, as many as fit
+        int so = 0;
+        if (precision == EWALD_FP64) {
+            e = s.dim == 3 ? allow_smem(k_sfac_listed<double, 3>, cfg->sfac_smem) : allow_smem(k_sfac_listed<double, 2>, cfg->sfac_smem);
+            if (!e) e = s.dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&so, k_sfac_listed<double, 3>, s.sfac_threads, cfg->sfac_smem)
+                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&so, k_sfac_listed<double, 2>, s.sfac_threads, cfg->sfac_smem);
+        } else {
+            e = s.dim == 3 ? allow_smem(k_sfac_listed<float, 3>, cfg->sfac_smem) : allow_smem(k_sfac_listed<float, 2>, cfg->sfac_smem);
+            if (!e) e = s.dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&so, k_sfac_listed<float, 3>, s.sfac_threads, cfg->sfac_smem)
+                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&so, k_sfac_listed<float, 2>, s.sfac_threads, cfg->sfac_smem);
+        }
+        if (e) return e;
+        cfg->sfac_grid = cfg->sm_count * std::max(so, 1);
+    }
     int occ = 0;
     if (s.tier2_f > 0) {  // tiered FP64: FP64 structure factor, tiered real space
         if (s.dim == 3) {
@@ -189,6 +218,9 @@ int configure_launch(SysDev &s, int precision, LaunchCfg *cfg) {
     if (e) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     cfg->real_grid = cfg->sm_count * occ;
+    cfg->propose_grid = 0;
+    if (precision == EWALD_MIXED && (e = (cudaError_t)configure_propose_mixed(s, cfg->sm_count, &cfg->propose_grid)))
+        return e;
     cfg->move_smem = move_smem_bytes(s, precision);
     return configure_move(s, precision, cfg->move_smem);
 }
@@ -219,6 +251,17 @@ int launch_sfac(const SysDev &s, const BatchDev &b, int precision, const LaunchC
     } else {
         if (s.dim == 3) k_sfac<float, 3><<<grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
         else k_sfac<float, 2><<<grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, only, cfg.sfac_te, we);
+    }
+    return cudaGetLastError();
+}
+
+int launch_sfac_listed(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg, cudaStream_t st) {
+    if (precision == EWALD_FP64) {
+        if (s.dim == 3) k_sfac_listed<double, 3><<<cfg.sfac_grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, cfg.sfac_te);
+        else k_sfac_listed<double, 2><<<cfg.sfac_grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, cfg.sfac_te);
+    } else {
+        if (s.dim == 3) k_sfac_listed<float, 3><<<cfg.sfac_grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, cfg.sfac_te);
+        else k_sfac_listed<float, 2><<<cfg.sfac_grid, s.sfac_threads, cfg.sfac_smem, st>>>(s, b, cfg.sfac_te);
     }
     return cudaGetLastError();
 }

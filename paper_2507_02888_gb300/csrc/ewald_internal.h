@@ -123,6 +123,7 @@ struct BatchDev {
     unsigned long long *pend_u;  // [W][3]
     int *acc_count;              // [W]
     unsigned char *resum_flag;   // [W]
+    int *resum_list;             // [1 + W]: count, then the walkers to re-sum (mixed accept; may be null)
     double *part_real;           // [W][n_items]
     double *part_recip;          // [W][n_gchunks]
     double *e;                   // [W]
@@ -176,6 +177,8 @@ struct LaunchCfg {
     int real_grid;      // persistent grid of the real-space kernel
     size_t real_smem, sfac_smem, move_smem;
     int sfac_te;        // electrons per structure-factor tile
+    int sfac_grid;      // persistent grid of the listed (re-sum) structure factor
+    int propose_grid;   // persistent grid of the mixed-precision propose kernel
 };
 int configure_launch(SysDev &s, int precision, LaunchCfg *cfg);
 int launch_ingest(const SysDev &s, const BatchDev &b, const double *pos, cudaStream_t st);
@@ -189,6 +192,12 @@ int launch_propose(const SysDev &s, const BatchDev &b, int precision, const Laun
                    const int *k, const double *r_new, double *de, cudaStream_t st);
 int launch_accept(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg,
                   const unsigned char *acc, int resum_every, cudaStream_t st);
+// move_mixed.cu: the mixed-precision propose kernel (persistent CTAs)
+int configure_propose_mixed(const SysDev &s, int sm_count, int *grid);
+int launch_propose_mixed(const SysDev &s, const BatchDev &b, int grid, const int *k, const double *r_new, double *de,
+                         cudaStream_t st);
+// rho(G) of the walkers in b.resum_list (after a mixed-precision accept)
+int launch_sfac_listed(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg, cudaStream_t st);
 
 // Polynomial two-body Jastrow term u (jastrow_u.cu): device tables.
 struct JuDev {

@@ -108,6 +108,61 @@ __global__ void __launch_bounds__(kMoveThreads)
     }
 }
 
+// Mixed precision accept, one thread per (G slot, walker): rho(G) += delta(G)
+// with delta = q_k (e^{iG.r'} - e^{iG.r}) from exact fixed-point phases (one
+// sincospi each), added by the two-sum of RhoIO<float>; every slot of every
+// accepted walker at once, so the read-modify-write of rho streams at full
+// width instead of following each thread's G run.  Positions and counters
+// follow in k_accept_finish (after every slot has read the old position).
+template <int DIM>
+__global__ void __launch_bounds__(256) k_accept_slots(SysDev s, BatchDev b, const unsigned char *__restrict__ acc) {
+    const int w = blockIdx.y;
+    const int k = b.pend_k[w];
+    if (k < 0 || !acc[w]) return;  // uniform over the CTA
+    const int slots = s.n_runs * s.run_len;
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= slots) return;
+    const int run = slot % s.n_runs, r = slot / s.n_runs;
+    const int4 rn = s.runs[run];
+    const int dir = rn.w < 0 ? -1 : 1;
+    if (r >= rn.w * dir) return;  // padding slot of a short run
+    const int n[3] = {rn.x + dir * r, rn.y, rn.z};
+    unsigned po = 0u, pn = 0u;  // n . u mod 2^32: exact phases of the old and new position
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        po += (unsigned)n[d] * (unsigned)(b.u[((size_t)w * DIM + d) * s.mob_stride + k] >> 32);
+        pn += (unsigned)n[d] * (unsigned)(b.pend_u[(size_t)w * 3 + d] >> 32);
+    }
+    float so, co, sn, cn;
+    FP<float>::sincospi2(FP<float>::frac(po), &so, &co);
+    FP<float>::sincospi2(FP<float>::frac(pn), &sn, &cn);
+    const float q = s.q_mob_f[k];
+    const int L = DIM == 2 && s.n_layers > 1 ? s.mob_layer[k] : 0;
+    double2 *rho = b.rho + ((size_t)w * s.n_layers + L) * slots;
+    RhoIO<float>::add(rho, slot, Cx<float>{q * (cn - co), q * (sn - so)});
+}
+
+// Position update and re-sum bookkeeping of an accept (one thread per
+// walker); walkers due for a re-sum are listed in b.resum_list.
+template <int DIM>
+__global__ void k_accept_finish(SysDev s, BatchDev b, const unsigned char *__restrict__ acc, int resum_every) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= b.W) return;
+    const int k = b.pend_k[w];
+    b.pend_k[w] = -1;
+    if (k < 0 || !acc[w]) {
+        b.resum_flag[w] = 0;
+        return;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) b.u[((size_t)w * DIM + d) * s.mob_stride + k] = b.pend_u[(size_t)w * 3 + d];
+    const int c = b.acc_count[w] + 1;
+    const bool f = c >= resum_every;
+    b.acc_count[w] = f ? 0 : c;
+    b.resum_flag[w] = f ? 1 : 0;
+    if (f) b.resum_list[1 + atomicAdd(b.resum_list, 1)] = w;
+}
+
 size_t move_smem_bytes(const SysDev &s, int precision) {
     return precision == EWALD_FP64 ? MoveSmem<double>::bytes(s) : MoveSmem<float>::bytes(s);
 }
@@ -137,6 +192,7 @@ int configure_move(const SysDev &s, int precision, size_t smem) {
 
 int launch_propose(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg, const int *k,
                    const double *r_new, double *de, cudaStream_t st) {
+    if (precision == EWALD_MIXED && cfg.propose_grid > 0) return launch_propose_mixed(s, b, cfg.propose_grid, k, r_new, de, st);
     if (precision == EWALD_FP64) {
         if (s.dim == 3) k_propose<double, 3><<<b.W, kMoveThreads, cfg.move_smem, st>>>(s, b, k, r_new, de);
         else k_propose<double, 2><<<b.W, kMoveThreads, cfg.move_smem, st>>>(s, b, k, r_new, de);
@@ -149,6 +205,19 @@ int launch_propose(const SysDev &s, const BatchDev &b, int precision, const Laun
 
 int launch_accept(const SysDev &s, const BatchDev &b, int precision, const LaunchCfg &cfg,
                   const unsigned char *acc, int resum_every, cudaStream_t st) {
+    if (precision != EWALD_FP64 && b.resum_list) {
+        cudaError_t e = cudaMemsetAsync(b.resum_list, 0, sizeof(int), st);
+        if (e) return e;
+        const dim3 grid((s.n_runs * s.run_len + 255) / 256, b.W);
+        if (s.dim == 3) {
+            k_accept_slots<3><<<grid, 256, 0, st>>>(s, b, acc);
+            k_accept_finish<3><<<(b.W + 127) / 128, 128, 0, st>>>(s, b, acc, resum_every);
+        } else {
+            k_accept_slots<2><<<grid, 256, 0, st>>>(s, b, acc);
+            k_accept_finish<2><<<(b.W + 127) / 128, 128, 0, st>>>(s, b, acc, resum_every);
+        }
+        return cudaGetLastError();
+    }
     if (precision == EWALD_FP64) {
         if (s.dim == 3) k_accept<double, 3><<<b.W, kMoveThreads, cfg.move_smem, st>>>(s, b, acc, resum_every);
         else k_accept<double, 2><<<b.W, kMoveThreads, cfg.move_smem, st>>>(s, b, acc, resum_every);
