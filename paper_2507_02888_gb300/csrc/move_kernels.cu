@@ -108,59 +108,73 @@ __global__ void __launch_bounds__(kMoveThreads)
     }
 }
 
-// Mixed precision accept, one thread per (G slot, walker): rho(G) += delta(G)
-// with delta = q_k (e^{iG.r'} - e^{iG.r}) from exact fixed-point phases (one
-// sincospi each), added by the two-sum of RhoIO<float>; every slot of every
-// accepted walker at once, so the read-modify-write of rho streams at full
-// width instead of following each thread's G run.  Positions and counters
-// follow in k_accept_finish (after every slot has read the old position).
+// Mixed precision accept: one CTA per walker, as k_accept, with each
+// thread's G run of rho(G) loaded before the recurrence updates it (the
+// loads of a run are independent, so up to kRunLen are in flight per
+// thread), the float-pair rho updated by two-sums, and walkers due for a
+// re-sum listed in b.resum_list.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_accept_slots(SysDev s, BatchDev b, const unsigned char *__restrict__ acc) {
-    const int w = blockIdx.y;
+__global__ void __launch_bounds__(kMoveThreads)
+    k_accept_mixed(SysDev s, BatchDev b, const unsigned char *__restrict__ acc, int resum_every) {
+    extern __shared__ __align__(32) unsigned char smem[];
+    MoveSmem<float> m;
+    m.carve(smem, s, DIM);
+    const int w = blockIdx.x, tid = threadIdx.x;
     const int k = b.pend_k[w];
-    if (k < 0 || !acc[w]) return;  // uniform over the CTA
-    const int slots = s.n_runs * s.run_len;
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= slots) return;
-    const int run = slot % s.n_runs, r = slot / s.n_runs;
-    const int4 rn = s.runs[run];
-    const int dir = rn.w < 0 ? -1 : 1;
-    if (r >= rn.w * dir) return;  // padding slot of a short run
-    const int n[3] = {rn.x + dir * r, rn.y, rn.z};
-    unsigned po = 0u, pn = 0u;  // n . u mod 2^32: exact phases of the old and new position
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        po += (unsigned)n[d] * (unsigned)(b.u[((size_t)w * DIM + d) * s.mob_stride + k] >> 32);
-        pn += (unsigned)n[d] * (unsigned)(b.pend_u[(size_t)w * 3 + d] >> 32);
-    }
-    float so, co, sn, cn;
-    FP<float>::sincospi2(FP<float>::frac(po), &so, &co);
-    FP<float>::sincospi2(FP<float>::frac(pn), &sn, &cn);
-    const float q = s.q_mob_f[k];
-    const int L = DIM == 2 && s.n_layers > 1 ? s.mob_layer[k] : 0;
-    double2 *rho = b.rho + ((size_t)w * s.n_layers + L) * slots;
-    RhoIO<float>::add(rho, slot, Cx<float>{q * (cn - co), q * (sn - so)});
-}
-
-// Position update and re-sum bookkeeping of an accept (one thread per
-// walker); walkers due for a re-sum are listed in b.resum_list.
-template <int DIM>
-__global__ void k_accept_finish(SysDev s, BatchDev b, const unsigned char *__restrict__ acc, int resum_every) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= b.W) return;
-    const int k = b.pend_k[w];
-    b.pend_k[w] = -1;
     if (k < 0 || !acc[w]) {
-        b.resum_flag[w] = 0;
+        if (tid == 0) {
+            b.pend_k[w] = -1;
+            b.resum_flag[w] = 0;
+        }
         return;
     }
+    unsigned uo[3], un[3];
+    for (int d = 0; d < 3; ++d) {
+        uo[d] = d < DIM ? (unsigned)(b.u[((size_t)w * DIM + d) * s.mob_stride + k] >> 32) : 0u;
+        un[d] = (unsigned)(b.pend_u[(size_t)w * 3 + d] >> 32);
+    }
+    build_move_tables<float, DIM>(s, uo, un, m.tab);
+    __syncthreads();
+    const float qk = s.q_mob_f[k];
+    const size_t slots = (size_t)s.n_runs * s.run_len;
+    float4 *rho = (float4 *)(b.rho + ((size_t)w * s.n_layers + (DIM == 2 && s.n_layers > 1 ? s.mob_layer[k] : 0)) * slots);
+    const MoveTables<float> &t = m.tab;
+    for (int run = tid; run < s.n_runs; run += blockDim.x) {
+        const int4 rn = s.runs[run];
+        const int dir = rn.w < 0 ? -1 : 1, len = rn.w * dir;
+        float4 v[kRunLen];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) b.u[((size_t)w * DIM + d) * s.mob_stride + k] = b.pend_u[(size_t)w * 3 + d];
-    const int c = b.acc_count[w] + 1;
-    const bool f = c >= resum_every;
-    b.acc_count[w] = f ? 0 : c;
-    b.resum_flag[w] = f ? 1 : 0;
-    if (f) b.resum_list[1 + atomicAdd(b.resum_list, 1)] = w;
+        for (int r = 0; r < kRunLen; ++r)
+            if (r < len) v[r] = rho[(size_t)r * s.n_runs + run];
+        Cx<float> zo = cmul(t.P[0][0][rn.x + s.n1max], t.P[0][1][rn.y + s.n2max]);
+        Cx<float> zn = cmul(t.P[1][0][rn.x + s.n1max], t.P[1][1][rn.y + s.n2max]);
+        if (DIM == 3) {
+            zo = cmul(zo, t.P[0][2][rn.z]);
+            zn = cmul(zn, t.P[1][2][rn.z]);
+        }
+        const Cx<float> so = t.P[0][0][s.n1max + dir], sn = t.P[1][0][s.n1max + dir];
+#pragma unroll
+        for (int r = 0; r < kRunLen; ++r) {
+            if (r < len) {
+                float hx = v[r].x, lx = v[r].z, hy = v[r].y, ly = v[r].w;
+                RhoIO<float>::acc(hx, lx, qk * (zn.x - zo.x));
+                RhoIO<float>::acc(hy, ly, qk * (zn.y - zo.y));
+                rho[(size_t)r * s.n_runs + run] = make_float4(hx, hy, lx, ly);
+                zo = cmul(zo, so);
+                zn = cmul(zn, sn);
+            }
+        }
+    }
+    __syncthreads();  // every thread has read the old position
+    if (tid < DIM) b.u[((size_t)w * DIM + tid) * s.mob_stride + k] = b.pend_u[(size_t)w * 3 + tid];
+    if (tid == 0) {
+        b.pend_k[w] = -1;
+        const int c = b.acc_count[w] + 1;
+        const bool f = c >= resum_every;
+        b.acc_count[w] = f ? 0 : c;
+        b.resum_flag[w] = f ? 1 : 0;
+        if (f) b.resum_list[1 + atomicAdd(b.resum_list, 1)] = w;
+    }
 }
 
 size_t move_smem_bytes(const SysDev &s, int precision) {
@@ -181,9 +195,11 @@ int configure_move(const SysDev &s, int precision, size_t smem) {
     } else {
         if (s.dim == 3) {
             if ((e = set((const void *)k_propose<float, 3>))) return e;
+            if ((e = set((const void *)k_accept_mixed<3>))) return e;
             e = set((const void *)k_accept<float, 3>);
         } else {
             if ((e = set((const void *)k_propose<float, 2>))) return e;
+            if ((e = set((const void *)k_accept_mixed<2>))) return e;
             e = set((const void *)k_accept<float, 2>);
         }
     }
@@ -208,14 +224,8 @@ int launch_accept(const SysDev &s, const BatchDev &b, int precision, const Launc
     if (precision != EWALD_FP64 && b.resum_list) {
         cudaError_t e = cudaMemsetAsync(b.resum_list, 0, sizeof(int), st);
         if (e) return e;
-        const dim3 grid((s.n_runs * s.run_len + 255) / 256, b.W);
-        if (s.dim == 3) {
-            k_accept_slots<3><<<grid, 256, 0, st>>>(s, b, acc);
-            k_accept_finish<3><<<(b.W + 127) / 128, 128, 0, st>>>(s, b, acc, resum_every);
-        } else {
-            k_accept_slots<2><<<grid, 256, 0, st>>>(s, b, acc);
-            k_accept_finish<2><<<(b.W + 127) / 128, 128, 0, st>>>(s, b, acc, resum_every);
-        }
+        if (s.dim == 3) k_accept_mixed<3><<<b.W, kMoveThreads, cfg.move_smem, st>>>(s, b, acc, resum_every);
+        else k_accept_mixed<2><<<b.W, kMoveThreads, cfg.move_smem, st>>>(s, b, acc, resum_every);
         return cudaGetLastError();
     }
     if (precision == EWALD_FP64) {

@@ -20,6 +20,9 @@
 namespace ewald {
 
 constexpr int kProposeMixedThreads = 256;
+// pending terms per lane: a walker's move gives each lane ~25 terms, so a
+// short ring (with weights: +-q_k q_j) keeps the CTA small
+constexpr int kMoveRing = 16;
 
 struct ProposeMixedSmem {
     MixedImageSmem ims;
@@ -27,7 +30,7 @@ struct ProposeMixedSmem {
     MoveTables<float> tab;
     double *red;
     __host__ __device__ static size_t ring_bytes() {
-        return align16((size_t)(kProposeMixedThreads / 32) * kLaneRing * 32 * sizeof(float) * 2);
+        return align16((size_t)(kProposeMixedThreads / 32) * kMoveRing * 32 * sizeof(float) * 2);
     }
     __host__ __device__ static size_t bytes(const SysDev &s) {
         return MixedImageSmem::bytes(s, s.dim) + ring_bytes() + MoveSmem<float>::table_bytes(s) +
@@ -70,13 +73,33 @@ __device__ inline double close_term_moved(const SysDev &s, const BatchDev &b, in
     return close_term<DIM>(s, dd, img, wgt, b.status, z2);
 }
 
+// The proposals checked and converted, one thread per walker: the moved
+// particle's index, its new position as fixed-point fractions (pend_u) and
+// a flag on a bad index or a non-finite position (pend_k = -1, dE = NaN).
+template <int DIM>
+__global__ void k_propose_prepare(SysDev s, BatchDev b, const int *__restrict__ kk, const double *__restrict__ r_new,
+                                  double *__restrict__ de) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= b.W) return;
+    const int k = kk[w];
+    unsigned long long un[3] = {0, 0, 0};
+    bool ok = k >= 0 && k < s.n_mob;
+    ok = cart_to_fixed<DIM>(s, r_new + (size_t)w * DIM, un) && ok;
+    if (!ok) {
+        atomicOr(b.status, ST_BAD_INDEX);
+        b.pend_k[w] = -1;
+        de[w] = __longlong_as_double(0x7ff8000000000000LL);  // NaN
+        return;
+    }
+    b.pend_k[w] = k;
+    for (int d = 0; d < 3; ++d) b.pend_u[(size_t)w * 3 + d] = un[d];
+}
+
 template <int DIM, int CM>
 __global__ void __launch_bounds__(kProposeMixedThreads)
-    k_propose_mixed(SysDev s, BatchDev b, const int *__restrict__ kk, const double *__restrict__ r_new,
-                    double *__restrict__ de) {
+    k_propose_mixed(SysDev s, BatchDev b, double *__restrict__ de) {
     extern __shared__ __align__(32) unsigned char smem[];
-    __shared__ int sk;
-    __shared__ unsigned long long su[2][3];  // old, new
+    __shared__ unsigned long long su[2][3];  // old, new: exact fixed-point coordinates
     ProposeMixedSmem m;
     m.carve(smem, s, DIM);
     m.ims.stage(s, DIM);
@@ -85,31 +108,14 @@ __global__ void __launch_bounds__(kProposeMixedThreads)
     const int n_other = s.n_mob - 1 + s.n_fix;
     for (int w = blockIdx.x; w < b.W; w += gridDim.x) {
         __syncthreads();  // the previous walker is done with the shared state
-        if (tid == 0) {
-            const int k = kk[w];
-            unsigned long long un[3] = {0, 0, 0};
-            bool ok = k >= 0 && k < s.n_mob;
-            ok = cart_to_fixed<DIM>(s, r_new + (size_t)w * DIM, un) && ok;
-            if (!ok) {
-                atomicOr(b.status, ST_BAD_INDEX);
-                b.pend_k[w] = -1;
-                sk = -1;
-            } else {
-                b.pend_k[w] = k;
-                for (int d = 0; d < 3; ++d) {
-                    b.pend_u[(size_t)w * 3 + d] = un[d];
-                    su[1][d] = un[d];
-                    su[0][d] = d < DIM ? b.u[((size_t)w * DIM + d) * s.mob_stride + k] : 0;
-                }
-                sk = k;
-            }
+        const int k = b.pend_k[w];
+        if (k < 0) continue;  // a bad proposal (k_propose_prepare set dE = NaN)
+        if (tid < 6) {
+            const int which = tid / 3, d = tid % 3;
+            su[which][d] = which ? b.pend_u[(size_t)w * 3 + d]
+                                 : (d < DIM ? b.u[((size_t)w * DIM + d) * s.mob_stride + k] : 0ull);
         }
         __syncthreads();
-        const int k = sk;
-        if (k < 0) {
-            if (tid == 0) de[w] = __longlong_as_double(0x7ff8000000000000LL);  // NaN
-            continue;
-        }
         unsigned uo[3], un[3];
         for (int d = 0; d < 3; ++d) {
             uo[d] = (unsigned)(su[0][d] >> 32);
@@ -123,21 +129,35 @@ __global__ void __launch_bounds__(kProposeMixedThreads)
         const unsigned u2o = DIM == 2 ? (layered ? __float_as_uint(zk) : 0u) : uo[2];
         const unsigned u2n = DIM == 2 ? (layered ? __float_as_uint(zk) : 0u) : un[2];
         // real space: slot t = (other particle jj, old/new) over the CTA's lanes
-        LaneRing<true> ring{m.rings + (size_t)warp * kLaneRing * 32 * 2 + lane, 0u, 0u};
+        LaneRing<true, kMoveRing> ring{m.rings + (size_t)warp * kMoveRing * 32 * 2 + lane, 0u, 0u};
         Acc<float> acc;
         double acc64 = 0.0;
+        // slot t: the other particle of index jj (mobile ones except k, then
+        // the fixed ones) at the old (t even) or new (t odd) position of k;
+        // each lane loads its next slot's particle while it works on this one
+        auto other = [&](int t, int &j, bool &fixedj) {
+            const int jj = t >> 1;
+            fixedj = jj >= s.n_mob - 1;
+            j = fixedj ? jj - (s.n_mob - 1) : (jj < k ? jj : jj + 1);
+            Tile16 p = {{0u, 0u, 0u}, 0.0f};
+            if (t < 2 * n_other) p = fixedj ? tile16_fixed<DIM>(s, j) : tile16_mobile<DIM>(s, b, w, j);
+            return p;
+        };
+        int jn;
+        bool fn;
+        Tile16 pn = other(warp * 32 + lane, jn, fn);
         for (int base = warp * 32; base < 2 * n_other; base += blockDim.x) {
             const int t = base + lane;
             const bool v = t < 2 * n_other;
-            const int jj = t >> 1, which = t & 1;
-            const bool fixedj = jj >= s.n_mob - 1;
-            const int j = fixedj ? jj - (s.n_mob - 1) : (jj < k ? jj : jj + 1);
-            Tile16 pj = {{0u, 0u, 0u}, 0.0f};
-            if (v) pj = fixedj ? tile16_fixed<DIM>(s, j) : tile16_mobile<DIM>(s, b, w, j);
+            const int which = t & 1;
+            const Tile16 pj = pn;
+            const int j = jn;
+            const bool fixedj = fn;
+            pn = other(base + blockDim.x + lane, jn, fn);
             const float wgt = (which ? 1.0f : -1.0f) * qk * pj.q;
             const Tile16 pkw = which ? Tile16{{un[0], un[1], u2n}, qk} : Tile16{{uo[0], uo[1], u2o}, qk};
             bool close = false;
-            pair_ring<DIM, CM, true>(s, m.ims, pkw, pj, v, wgt, ring, close, acc, tk);
+            pair_ring<DIM, CM, true, kMoveRing>(s, m.ims, pkw, pj, v, wgt, ring, close, acc, tk);
             if (__any_sync(0xffffffffu, close) && close) {  // rare: the FP64 term now
                 float x[DIM], z2;
                 const int sc = pair_cart<DIM>(s, pkw, pj, x, z2);
@@ -164,7 +184,7 @@ __global__ void __launch_bounds__(kProposeMixedThreads)
     }
 }
 
-using ProposeFn = void (*)(SysDev, BatchDev, const int *, const double *, double *);
+using ProposeFn = void (*)(SysDev, BatchDev, double *);
 
 template <int DIM>
 static ProposeFn propose_fn(int cm) {
@@ -197,8 +217,9 @@ int configure_propose_mixed(const SysDev &s, int sm_count, int *grid) {
 
 int launch_propose_mixed(const SysDev &s, const BatchDev &b, int grid, const int *k, const double *r_new, double *de,
                          cudaStream_t st) {
-    propose_mixed_fn(s)<<<std::min(grid, b.W), kProposeMixedThreads, ProposeMixedSmem::bytes(s), st>>>(s, b, k, r_new,
-                                                                                                        de);
+    if (s.dim == 3) k_propose_prepare<3><<<(b.W + 127) / 128, 128, 0, st>>>(s, b, k, r_new, de);
+    else k_propose_prepare<2><<<(b.W + 127) / 128, 128, 0, st>>>(s, b, k, r_new, de);
+    propose_mixed_fn(s)<<<std::min(grid, b.W), kProposeMixedThreads, ProposeMixedSmem::bytes(s), st>>>(s, b, de);
     return cudaGetLastError();
 }
 

@@ -129,16 +129,16 @@ __device__ inline double close_term_global(const SysDev &s, const BatchDev &b, i
 // One warp's pending terms: lane l's entries k live at r2[k * 32] (and, with
 // weights, at r2[kLaneRing * 32 + k * 32]) of its column; cnt counts the
 // entries pushed, hd those evaluated (even, except after the final drain).
-template <bool QW>
+template <bool QW, int CAP = kLaneRing>
 struct LaneRing {
     float *col;      // this lane's column
     unsigned cnt, hd;
-    __device__ float *at(unsigned k) const { return col + (k & (kLaneRing - 1)) * 32; }
+    __device__ float *at(unsigned k) const { return col + (k & (CAP - 1)) * 32; }
     __device__ void push(bool pass, float r2, float wgt) {
         float *e = at(cnt);
         if (pass) {
             e[0] = r2;
-            if (QW) e[kLaneRing * 32] = wgt;
+            if (QW) e[CAP * 32] = wgt;
         }
         cnt += pass ? 1u : 0u;
     }
@@ -146,7 +146,7 @@ struct LaneRing {
     __device__ void eval_two(Acc<float> &acc, const TermK32 &tk) {
         const float *e = at(hd);
         float2 t = erfc_over_r_f32x2(make_float2(e[0], e[32]), tk);
-        if (QW) t = mul2(t, make_float2(e[kLaneRing * 32], e[kLaneRing * 32 + 32]));
+        if (QW) t = mul2(t, make_float2(e[CAP * 32], e[CAP * 32 + 32]));
         acc.add2(t);
         hd += 2;
     }
@@ -157,7 +157,7 @@ struct LaneRing {
         const float2 r2 = take ? make_float2(e[0], e[32]) : make_float2(1.0f, 1.0f);
         float2 t = erfc_over_r_f32x2(r2, tk);
         if (take) {
-            if (QW) t = mul2(t, make_float2(e[kLaneRing * 32], e[kLaneRing * 32 + 32]));
+            if (QW) t = mul2(t, make_float2(e[CAP * 32], e[CAP * 32 + 32]));
             acc.add2(t);
             hd += 2;
         }
@@ -171,7 +171,7 @@ struct LaneRing {
         const unsigned lo = __reduce_min_sync(0xffffffffu, pend);
         for (unsigned n = lo >> 1; n > 0; --n) eval_two(acc, tk);
         unsigned hi = __reduce_max_sync(0xffffffffu, cnt - hd);
-        while (hi > (unsigned)(kLaneRing - ROOM)) {
+        while (hi > (unsigned)(CAP - ROOM)) {
             eval_some(acc, tk);
             hi = __reduce_max_sync(0xffffffffu, cnt - hd);
         }
@@ -183,7 +183,7 @@ struct LaneRing {
             const float *e0 = at(hd), *e1 = at(hd + 1);
             float2 r2 = make_float2(n > 0 ? e0[0] : 1.0f, n > 1 ? e1[0] : 1.0f);
             float2 t = erfc_over_r_f32x2(r2, tk);
-            if (QW) t = mul2(t, make_float2(n > 0 ? e0[kLaneRing * 32] : 0.0f, n > 1 ? e1[kLaneRing * 32] : 0.0f));
+            if (QW) t = mul2(t, make_float2(n > 0 ? e0[CAP * 32] : 0.0f, n > 1 ? e1[CAP * 32] : 0.0f));
             if (n == 1) t.y = 0.0f;
             if (n > 0) acc.add2(t);
             hd += n;
@@ -234,9 +234,9 @@ __device__ __forceinline__ float4 lds128(const float4 *p) {
 // r^2 that pass; FIRST: the pairs start with candidate 0, the only image
 // through which a displacement of the cell can come within the close
 // radius: a close pair is recorded for FP64 instead.
-template <int DIM, int NP, bool FIRST, bool QW>
+template <int DIM, int NP, bool FIRST, bool QW, int CAP>
 __device__ __forceinline__ void test_pairs(const float4 *xy, const float2 *zz, const float *x, float z2, float rc2,
-                                           float close2, float wgt, LaneRing<QW> &ring, bool &close) {
+                                           float close2, float wgt, LaneRing<QW, CAP> &ring, bool &close) {
     const float2 x0 = splat(x[0]), x1 = splat(x[1]), zs = splat(z2);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -271,10 +271,10 @@ __host__ __device__ inline int mixed_pairs(int cand_max) {
 
 // The images of one pair of particles: CM candidate slots (CM = 2 ... 8
 // compile-time; CM = 0: the list in chunks of 4 pairs)
-template <int DIM, int CM, bool QW>
+template <int DIM, int CM, bool QW, int CAP>
 __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem &ims, const Tile16 &a,
-                                          const Tile16 &b, bool valid, float wgt, LaneRing<QW> &ring, bool &close,
-                                          Acc<float> &acc, const TermK32 &tk) {
+                                          const Tile16 &b, bool valid, float wgt, LaneRing<QW, CAP> &ring,
+                                          bool &close, Acc<float> &acc, const TermK32 &tk) {
     float x[DIM], z2;
     const int sc = pair_cart<DIM>(s, a, b, x, z2);
     const float rc2 = valid ? s.rc2_f : 0.0f;  // invalid lanes never pass
@@ -282,14 +282,14 @@ __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem 
     const float4 *xy = ims.xy + base;
     const float2 *zz = ims.z + base;
     if (CM > 0) {
-        test_pairs<DIM, CM / 2, true, QW>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
+        test_pairs<DIM, CM / 2, true, QW, CAP>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
         ring.template service<CM>(acc, tk);
     } else {
-        test_pairs<DIM, 4, true, QW>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
+        test_pairs<DIM, 4, true, QW, CAP>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
         ring.template service<8>(acc, tk);
         for (int ch = 4; ch < s.cand_pairs; ch += 4) {
             bool unused;
-            test_pairs<DIM, 4, false, QW>(xy + ch, zz + ch, x, z2, rc2, s.close2_f, wgt, ring, unused);
+            test_pairs<DIM, 4, false, QW, CAP>(xy + ch, zz + ch, x, z2, rc2, s.close2_f, wgt, ring, unused);
             ring.template service<8>(acc, tk);
         }
     }
@@ -365,7 +365,7 @@ __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, in
             const bool valid = vi && (!self || lane < jj);
             const float wgt = QW ? pi.q * pj.q : 1.0f;
             bool close = false;
-            pair_ring<DIM, CM, QW>(s, ims, pi, pj, valid, wgt, ring, close, acc, tk);
+            pair_ring<DIM, CM, QW, kLaneRing>(s, ims, pi, pj, valid, wgt, ring, close, acc, tk);
             const unsigned cb = __ballot_sync(0xffffffffu, close);
             if (cb) {  // uniform over the warp, rare
                 const int at = cl.n + __popc(cb & ((1u << lane) - 1u));
