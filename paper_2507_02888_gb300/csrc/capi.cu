@@ -919,7 +919,14 @@ int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
             }
         }
     }
-    std::stable_sort(items.begin(), items.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
+    // grouped by batch (a CTA then re-stages a system's tables about once per
+    // batch), the batch with the longest items first, longest first within one
+    std::vector<double> top(n, 0.0);
+    for (const It &x : items) top[x.d.y] = std::max(top[x.d.y], x.cost);
+    std::stable_sort(items.begin(), items.end(), [&](const It &x, const It &y) {
+        if (x.d.y != y.d.y) return top[x.d.y] != top[y.d.y] ? top[x.d.y] > top[y.d.y] : x.d.y < y.d.y;
+        return x.cost > y.cost;
+    });
     std::vector<int4> id(items.size());
     for (size_t k = 0; k < items.size(); ++k) id[k] = items[k].d;
 

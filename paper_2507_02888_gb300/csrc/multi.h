@@ -6,9 +6,13 @@
 
 namespace ewald {
 
-constexpr int kMultiThreads = 256;
+// threads per CTA: the FP32 kernel takes the mixed real-space loop's 16
+// warps (real_mixed.cuh), the FP64 one 8
+constexpr int kMultiThreads32 = 512, kMultiThreads64 = 256;
+template <typename R>
+constexpr int kMultiThreadsOf = sizeof(R) == 4 ? kMultiThreads32 : kMultiThreads64;
 // resident CTAs per SM the register budget is sized for (FP32, FP64 path)
-constexpr int kMultiMinBlocks32 = 3, kMultiMinBlocks64 = 2;
+constexpr int kMultiMinBlocks32 = 2, kMultiMinBlocks64 = 2;
 enum : int { kItemSfac = 0, kItemReal = 1 };
 
 struct MultiDev {

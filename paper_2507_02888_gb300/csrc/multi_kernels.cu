@@ -26,26 +26,29 @@ __device__ inline void cta_copy(T *dst, const T *src) {
 }
 
 // j slices per 32 x 32 sub-tile of a pair item, so that the item has at
-// least as many work units as the CTA has warps (a property of the system
-// alone: results do not depend on the other systems of the launch)
+// least as many work units as the CTA has warps (FP32: four times as many,
+// so that diagonal items split evenly too; a property of the system alone:
+// results do not depend on the other systems of the launch)
+template <typename R>
 __device__ inline int multi_jsplit(const SysDev &s) {
-    const int S = s.tile / 32, per = S * S;
+    const int S = s.tile / 32, per = S * S, want = (kMultiThreadsOf<R> / 32) * (sizeof(R) == 4 ? 4 : 1);
     int js = 1;
-    while (per * js < kMultiThreads / 32 && js < 32) js *= 2;
+    while (per * js < want && js < 32) js *= 2;
     return js;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kMultiThreads, sizeof(R) == 4 ? kMultiMinBlocks32 : kMultiMinBlocks64) k_multi_energy(MultiDev m) {
+__global__ void __launch_bounds__(kMultiThreadsOf<R>, sizeof(R) == 4 ? kMultiMinBlocks32 : kMultiMinBlocks64)
+    k_multi_energy(MultiDev m) {
     extern __shared__ __align__(32) unsigned char smem[];
     __shared__ SysDev ss;
     __shared__ BatchDev sb;
-    __shared__ int s_item, s_last, s_img_sys;
+    __shared__ int s_item, s_last, s_img_sys, s_bat;
     // candidate tables: the FP64 loop's (ImageSmem) or the mixed loop's
     using Ims = typename std::conditional<sizeof(R) == 4, MixedImageSmem, ImageSmem<R>>::type;
     Ims ims;
     unsigned char *work = smem + m.img_bytes;
-    if (threadIdx.x == 0) s_img_sys = -1;
+    if (threadIdx.x == 0) s_img_sys = s_bat = -1;
     for (;;) {
         __syncthreads();  // the previous item is finished with shared memory
         if (threadIdx.x == 0) s_item = atomicAdd(m.next, 1);
@@ -54,8 +57,12 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(R) == 4 ? kMultiMinBlock
         if (it >= m.n_items) break;
         const int4 d = m.items[it];  // (kind, batch, walker, sub)
         const int sys = m.bat_sys[d.y];
-        cta_copy(&ss, m.sys + sys);
-        cta_copy(&sb, m.bat + d.y);
+        if (d.y != s_bat) {  // uniform over the CTA; items come grouped by batch
+            cta_copy(&ss, m.sys + sys);
+            cta_copy(&sb, m.bat + d.y);
+            __syncthreads();
+            if (threadIdx.x == 0) s_bat = d.y;
+        }
         __syncthreads();
         if (d.x == kItemReal && s_img_sys != sys) {  // uniform over the CTA
             ims.carve(smem, ss, ss.dim);
@@ -68,7 +75,7 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(R) == 4 ? kMultiMinBlock
             if (ss.dim == 3) sfac_item<R, 3>(ss, sb, d.z, d.w, ss.sfac_te, true, work);
             else sfac_item<R, 2>(ss, sb, d.z, d.w, ss.sfac_te, true, work);
         } else {
-            const int js = multi_jsplit(ss);
+            const int js = multi_jsplit<R>(ss);
             if constexpr (sizeof(R) == 4) {
                 if (ss.dim == 3) real_item_mixed<3>(ss, sb, d.z, d.w, ims, work, js);
                 else real_item_mixed<2>(ss, sb, d.z, d.w, ims, work, js);
@@ -96,9 +103,10 @@ size_t multi_energy_smem(const std::vector<SysDev> &sys, int precision, size_t *
     for (const SysDev &s : sys) {
         size_t ib = precision == EWALD_FP64 ? ImageSmem<double>::bytes(s, s.dim) : MixedImageSmem::bytes(s, s.dim);
         img = std::max(img, ib);
-        work = std::max(work, sfac_bytes(s, precision, s.sfac_te, kMultiThreads));
-        work = std::max(work, precision == EWALD_FP64 ? real_work_bytes(s, precision, kMultiThreads / 32)
-                                                      : mixed_real_work_bytes(s, kMultiThreads / 32));
+        const int threads = precision == EWALD_FP64 ? kMultiThreads64 : kMultiThreads32;
+        work = std::max(work, sfac_bytes(s, precision, s.sfac_te, threads));
+        work = std::max(work, precision == EWALD_FP64 ? real_work_bytes(s, precision, threads / 32)
+                                                      : mixed_real_work_bytes(s, threads / 32));
     }
     *img_bytes = img;
     return img + work;
@@ -111,10 +119,10 @@ int configure_multi(int precision, size_t smem, int *grid) {
     if (e) return e;
     if (precision == EWALD_FP64) {
         if ((e = allow_max_smem(k_multi_energy<double>, smem))) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_energy<double>, kMultiThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_energy<double>, kMultiThreads64, smem);
     } else {
         if ((e = allow_max_smem(k_multi_energy<float>, smem))) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_energy<float>, kMultiThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_multi_energy<float>, kMultiThreads32, smem);
     }
     if (e) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
@@ -127,8 +135,8 @@ int launch_multi_energy(const MultiDev &m, int precision, int grid, size_t smem,
     if (!e) e = cudaMemsetAsync(m.done, 0, sizeof(int) * (size_t)m.n_walkers, st);
     if (e) return e;
     const int g = std::min(grid, std::max(m.n_items, 1));
-    if (precision == EWALD_FP64) k_multi_energy<double><<<g, kMultiThreads, smem, st>>>(m);
-    else k_multi_energy<float><<<g, kMultiThreads, smem, st>>>(m);
+    if (precision == EWALD_FP64) k_multi_energy<double><<<g, kMultiThreads64, smem, st>>>(m);
+    else k_multi_energy<float><<<g, kMultiThreads32, smem, st>>>(m);
     return cudaGetLastError();
 }
 
