@@ -819,6 +819,7 @@ int ewald_get_timing(ewald_ctx *c, double *ms, long long *launches) {
 // ------------------------------------------------------------------ multi
 
 struct ewald_multi {
+    ewald::MultiFn fn = nullptr;  // the energy kernel for these systems
     std::vector<ewald_batch *> batches;
     std::vector<ewald_ctx *> ctxs;        // distinct contexts, in first-use order
     int precision = 0;
@@ -874,7 +875,16 @@ int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
         if (si < 0) {
             si = (int)m->ctxs.size();
             m->ctxs.push_back(b->ctx);
-            sys.push_back(b->ctx->s);
+            SysDev sd = b->ctx->s;
+            // the FP32 launch has CTAs of kMultiThreads32 threads: its
+            // structure-factor items take as many G runs as fit (chunks of
+            // the context merged), so that no thread of the CTA idles
+            if (m->precision != EWALD_FP64)
+                while (sd.n_gchunks > 1 && 2 * sd.sfac_threads <= kMultiThreads32) {
+                    sd.sfac_threads *= 2;
+                    sd.n_gchunks = (sd.n_runs + sd.sfac_threads - 1) / sd.sfac_threads;
+                }
+            sys.push_back(sd);
         }
         m->batches.push_back(b);
         bat.push_back(b->b);
@@ -961,7 +971,8 @@ int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
     md.n_items = (int)id.size();
     md.n_walkers = nw;
     m->smem = multi_energy_smem(sys, m->precision, &md.img_bytes);
-    if (!e) chk((cudaError_t)configure_multi(m->precision, m->smem, &m->grid), "configure");
+    m->fn = multi_kernel(m->precision, sys);
+    if (!e) chk((cudaError_t)configure_multi(m->fn, m->precision, m->smem, &m->grid), "configure");
     if (!e) chk(cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming), "event");
     for (size_t k = 0; k < m->ctxs.size() && !e; ++k) {
         cudaEvent_t ev;
@@ -973,7 +984,7 @@ int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
         cudaGraph_t g = nullptr;
         chk(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         if (!e) {
-            int le = launch_multi_energy(md, m->precision, m->grid, m->smem, m->stream);
+            int le = launch_multi_energy(m->fn, md, m->precision, m->grid, m->smem, m->stream);
             cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
             chk((cudaError_t)le, "launch in capture");
             chk(ce, "end capture");

@@ -28,8 +28,14 @@ struct MultiDev {
     double *e_all;         // [n_walkers] energies
 };
 
+using MultiFn = void (*)(MultiDev);
 size_t multi_energy_smem(const std::vector<SysDev> &sys, int precision, size_t *img_bytes);
-int configure_multi(int precision, size_t smem, int *grid);
-int launch_multi_energy(const MultiDev &m, int precision, int grid, size_t smem, cudaStream_t st);
+MultiFn multi_kernel(int precision, const std::vector<SysDev> &sys);
+// multi_spec.cu: the FP32 kernel specialized for systems of one dimension
+// with uniform charges and candidate slot counts cma, cmb; null if none is
+// compiled for that composition
+MultiFn multi_kernel_spec(int dim, int cma, int cmb);
+int configure_multi(MultiFn f, int precision, size_t smem, int *grid);
+int launch_multi_energy(MultiFn f, const MultiDev &m, int precision, int grid, size_t smem, cudaStream_t st);
 
 }  // namespace ewald
