@@ -267,8 +267,10 @@ const char *ewald_server_error_message(const ewald_server *srv);
 /* Autotuner.  Times the real-space kernel on (up to 512 of) the batch's
  * walkers for every allowed real-space tiling - pair tiles of 32, 64 or 128
  * particles per side (also 256 in the mixed form) x 2^bits displacement
- * cells per axis (candidate lists
- * <= 48 KB) - and keeps the fastest in the batch's context.  With
+ * cells per axis (candidate lists <= 48 KB) x, in the mixed form, CTAs of
+ * 256 or 512 threads - and the structure-factor kernel for 1 to 4 chunks of
+ * G runs per walker (the threads of its CTAs), and keeps the fastest of
+ * each in the batch's context.  With
  * cache_path (may be NULL) the result is looked up first and stored after
  * tuning in a small JSON file keyed by the system's shape and the GPU name;
  * ewald_create also applies a cached tiling when the environment variable
@@ -279,6 +281,9 @@ typedef struct {
     double ms;       /* real-space kernel time of the chosen tiling, ms */
     int n_tried;     /* tilings timed (0 if taken from the cache) */
     int from_cache;
+    int real_threads;  /* threads per real-space CTA of the chosen tiling */
+    int sfac_chunks;   /* structure-factor chunks per walker chosen */
+    double sfac_ms;    /* structure-factor kernel time with them, ms */
 } ewald_tune_result;
 int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *res);
 

@@ -32,6 +32,14 @@ unsigned long long to_fixed(double f) {
     return (unsigned long long)std::ldexp(f, 64);
 }
 
+// The structure factor in n_ch chunks of G runs per walker (whole warps,
+// at most kSfacThreads runs each; the launch configuration follows).
+void set_sfac_chunks(SysDev &s, int n_ch) {
+    n_ch = std::max(n_ch, (s.n_runs + kSfacThreads - 1) / kSfacThreads);
+    s.sfac_threads = std::min(kSfacThreads, ((s.n_runs + n_ch - 1) / n_ch + 31) / 32 * 32);
+    s.n_gchunks = (s.n_runs + s.sfac_threads - 1) / s.sfac_threads;
+}
+
 void free_one(std::vector<void *> &v, const void *p) {
     if (!p) return;
     for (size_t i = 0; i < v.size(); ++i)
@@ -107,6 +115,14 @@ int apply_tiling(ewald_ctx *c, int S, int bits) {
     return EWALD_OK;
 }
 
+// A tuned configuration: real-space tiling, the mixed form's CTA warps
+// (warps > 0) and the structure-factor chunks (chunks > 0).
+int apply_config(ewald_ctx *c, int S, int bits, int warps, int chunks) {
+    if (warps > 0) c->s.real_warps = warps;
+    if (chunks > 0) set_sfac_chunks(c->s, chunks);
+    return apply_tiling(c, S, bits);
+}
+
 int build_device(ewald_ctx *c) {
     HostTables &t = c->t;
     SysDev &s = c->s;
@@ -173,9 +189,9 @@ int build_device(ewald_ctx *c) {
     s.run_len = t.run_len;
     s.n_gh = (int)t.g2slot.size();
     // as few chunks as kSfacThreads allows, split evenly (whole warps)
-    const int n_ch = (s.n_runs + kSfacThreads - 1) / kSfacThreads;
-    s.sfac_threads = ((s.n_runs + n_ch - 1) / n_ch + 31) / 32 * 32;
-    s.n_gchunks = (s.n_runs + s.sfac_threads - 1) / s.sfac_threads;
+    set_sfac_chunks(s, (s.n_runs + kSfacThreads - 1) / kSfacThreads);
+    c->max_gchunks = (s.n_runs + 31) / 32;  // the finest chunking (32 runs each) sizes the partial sums
+    s.real_warps = kRealMixedWarps;
     s.n1max = std::max(t.n1max, 1);
     s.n2max = std::max(t.n2max, 1);
     s.n3max = std::max(t.n3max, 1);
@@ -424,6 +440,7 @@ std::string tune_key(const ewald_ctx *c) {
 struct TuneEntry {
     int tile, bits;
     double ms;
+    int warps = 0, chunks = 0;  // real-space CTA warps (mixed form), structure-factor chunks (0: default)
 };
 
 std::map<std::string, TuneEntry> read_tune_cache(const char *path) {
@@ -441,6 +458,8 @@ std::map<std::string, TuneEntry> read_tune_cache(const char *path) {
         if ((p = line.find("\"tile\": ", b)) != std::string::npos) e.tile = std::atoi(line.c_str() + p + 8);
         if ((p = line.find("\"bits\": ", b)) != std::string::npos) e.bits = std::atoi(line.c_str() + p + 8);
         if ((p = line.find("\"ms\": ", b)) != std::string::npos) e.ms = std::atof(line.c_str() + p + 6);
+        if ((p = line.find("\"warps\": ", b)) != std::string::npos) e.warps = std::atoi(line.c_str() + p + 9);
+        if ((p = line.find("\"chunks\": ", b)) != std::string::npos) e.chunks = std::atoi(line.c_str() + p + 10);
         if (e.tile == 32 || e.tile == 64 || e.tile == 128 || e.tile == 256) m[line.substr(a, b - a)] = e;
     }
     return m;
@@ -453,8 +472,9 @@ bool write_tune_cache(const char *path, const std::map<std::string, TuneEntry> &
     std::fprintf(f, "{\"entries\": [\n");
     size_t i = 0;
     for (auto &kv : m)
-        std::fprintf(f, "  {\"key\": \"%s\", \"tile\": %d, \"bits\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(),
-                     kv.second.tile, kv.second.bits, kv.second.ms, ++i < m.size() ? "," : "");
+        std::fprintf(f, "  {\"key\": \"%s\", \"tile\": %d, \"bits\": %d, \"warps\": %d, \"chunks\": %d, \"ms\": %.6f}%s\n",
+                     kv.first.c_str(), kv.second.tile, kv.second.bits, kv.second.warps, kv.second.chunks,
+                     kv.second.ms, ++i < m.size() ? "," : "");
     std::fprintf(f, "]}\n");
     std::fclose(f);
     return std::rename(tmp.c_str(), path) == 0;
@@ -528,7 +548,7 @@ int ewald_create(const ewald_desc *desc, void *cuda_stream, ewald_ctx **out) {
         auto cache = read_tune_cache(path);
         auto it = cache.find(tune_key(c));
         if (it != cache.end() && tiling_allowed(c, it->second.tile / 32, it->second.bits)) {
-            st = apply_tiling(c, it->second.tile / 32, it->second.bits);
+            st = apply_config(c, it->second.tile / 32, it->second.bits, it->second.warps, it->second.chunks);
             if (st) {
                 ewald_destroy(c);
                 return st;
@@ -624,7 +644,7 @@ int ewald_batch_create(ewald_ctx *c, int W, ewald_batch **out) {
     chk(dalloc(o, &d.resum_flag, W));
     chk(dalloc(o, &d.resum_list, (size_t)W + 1));
     chk(dalloc(o, &d.part_real, (size_t)W * std::max(c->max_items, s.n_items)));
-    chk(dalloc(o, &d.part_recip, (size_t)W * s.n_gchunks));
+    chk(dalloc(o, &d.part_recip, (size_t)W * std::max(c->max_gchunks, s.n_gchunks)));
     chk(dalloc(o, &d.e, W));
     chk(dalloc(o, &d.comp, (size_t)W * 5));
     chk(dalloc(o, &d.status, 1));
@@ -1057,68 +1077,99 @@ int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *re
     ewald_tune_result r{};
     auto it = cache.find(key);
     if (it != cache.end() && tiling_allowed(c, it->second.tile / 32, it->second.bits)) {
-        int st = apply_tiling(c, it->second.tile / 32, it->second.bits);
+        int st = apply_config(c, it->second.tile / 32, it->second.bits, it->second.warps, it->second.chunks);
         if (st) return st;
         r.pair_tile = it->second.tile;
         r.subcell_bits = it->second.bits;
         r.ms = it->second.ms;
         r.from_cache = 1;
+        r.real_threads = c->t.precision == EWALD_MIXED && !c->t.tiered ? 32 * c->s.real_warps : kRealThreads;
+        r.sfac_chunks = c->s.n_gchunks;
         if (res) *res = r;
         return EWALD_OK;
     }
-    // time the real-space kernel on up to 512 of this batch's walkers
+    // time the kernels on up to 512 of this batch's walkers
     BatchDev view = b->b;
     view.W = std::min(view.W, 512);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    double best = 1e300;
-    int bestS = c->s.tile / 32, bestBits = c->s.sub_bits;
-    const int Ss[4] = {1, 2, 4, 8};
-    for (int S : Ss)
-        for (int bits = 0; bits <= (c->t.dim == 3 ? 4 : 6); ++bits) {
-            if (!tiling_allowed(c, S, bits)) continue;
-            int st = apply_tiling(c, S, bits);
-            if (st) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return st;
-            }
-            double t_min = 1e300;
-            for (int rep = 0; rep < 3; ++rep) {
-                cudaEventRecord(e0, c->stream);
-                int le = launch_real(c->s, view, c->t.precision, c->cfg, c->stream);
-                cudaEventRecord(e1, c->stream);
-                cudaError_t ce = cudaEventSynchronize(e1);
-                if (le || ce) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return cuda_fail(c, le ? (cudaError_t)le : ce);
-                }
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) t_min = std::min(t_min, (double)ms);  // the first launch warms up
-            }
-            r.n_tried += 1;
-            if (t_min < best) {
-                best = t_min;
-                bestS = S;
-                bestBits = bits;
-            }
+    auto best_of_3 = [&](auto &&launch, double *t_min) -> int {
+        *t_min = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, c->stream);
+            int le = launch();
+            cudaEventRecord(e1, c->stream);
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (le || ce) return le ? le : (int)ce;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) *t_min = std::min(*t_min, (double)ms);  // the first launch warms up
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    int st = apply_tiling(c, bestS, bestBits);
-    if (st) return st;
+        return 0;
+    };
+    auto done = [&](int st) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+    };
+    const bool mixed = c->t.precision == EWALD_MIXED && !c->t.tiered;
+    double best = 1e300;
+    int bestS = c->s.tile / 32, bestBits = c->s.sub_bits, bestWarps = c->s.real_warps;
+    const int Ss[4] = {1, 2, 4, 8};
+    const int warps_opts[2] = {8, 16};
+    for (int S : Ss)
+        for (int bits = 0; bits <= (c->t.dim == 3 ? 4 : 6); ++bits)
+            for (int wi = mixed ? 0 : 1; wi < 2; ++wi) {
+                if (!tiling_allowed(c, S, bits)) continue;
+                int st = apply_config(c, S, bits, warps_opts[wi], 0);
+                if (st) return done(st);
+                double t_min;
+                int le = best_of_3([&] { return launch_real(c->s, view, c->t.precision, c->cfg, c->stream); }, &t_min);
+                if (le) return done(cuda_fail(c, (cudaError_t)le));
+                r.n_tried += 1;
+                if (t_min < best) {
+                    best = t_min;
+                    bestS = S;
+                    bestBits = bits;
+                    bestWarps = warps_opts[wi];
+                }
+            }
+    int st = apply_config(c, bestS, bestBits, bestWarps, 0);
+    if (st) return done(st);
+    // structure factor: 1 to 4 chunks of G runs per walker
+    double best_sf = 1e300;
+    int bestCh = c->s.n_gchunks, last_ng = -1;
+    for (int ch = 1; ch <= 4; ++ch) {
+        SysDev trial = c->s;
+        set_sfac_chunks(trial, ch);
+        if (trial.n_gchunks == last_ng || trial.n_gchunks > c->max_gchunks) continue;
+        last_ng = trial.n_gchunks;
+        if ((st = apply_config(c, bestS, bestBits, bestWarps, ch))) return done(st);
+        double t_min;
+        int le = best_of_3([&] { return run_sfac(c, view, c->t.precision, nullptr); }, &t_min);
+        if (le) return done(cuda_fail(c, (cudaError_t)le));
+        if (t_min < best_sf) {
+            best_sf = t_min;
+            bestCh = ch;
+        }
+    }
+    if ((st = apply_config(c, bestS, bestBits, bestWarps, bestCh))) return done(st);
     r.pair_tile = 32 * bestS;
     r.subcell_bits = bestBits;
     r.ms = best;
+    r.real_threads = mixed ? 32 * bestWarps : kRealThreads;
+    r.sfac_chunks = c->s.n_gchunks;
+    r.sfac_ms = best_sf;
     if (cache_path) {
-        cache[key] = TuneEntry{32 * bestS, bestBits, best};
+        TuneEntry te{32 * bestS, bestBits, best};
+        te.warps = mixed ? bestWarps : 0;
+        te.chunks = bestCh;
+        cache[key] = te;
         write_tune_cache(cache_path, cache);
     }
     if (res) *res = r;
-    return EWALD_OK;
+    return done(EWALD_OK);
 }
 
 }  // extern "C"

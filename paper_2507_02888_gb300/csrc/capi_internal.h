@@ -20,6 +20,7 @@ struct ewald_ctx {
     int *d_g2slot = nullptr;
     int n_batches = 0;        // live batches; the context outlives them
     int max_items = 0;        // pair-tile items per walker at the finest tiling
+    int max_gchunks = 0;      // structure-factor chunks per walker at the finest chunking
     bool destroy_pending = false;
     int last_error = EWALD_OK;
     std::string why;

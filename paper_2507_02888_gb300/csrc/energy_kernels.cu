@@ -147,7 +147,7 @@ static size_t real_smem(const SysDev &s, int precision) {
     if (s.tier2_f > 0)
         return ImageSmem<float>::bytes(s, s.dim) + align16((s.n_img + 1) * sizeof(float4)) +
                real_work_bytes(s, precision, kRealWarps, true);
-    if (precision != EWALD_FP64) return MixedImageSmem::bytes(s, s.dim) + mixed_real_work_bytes(s, kRealMixedWarps);
+    if (precision != EWALD_FP64) return MixedImageSmem::bytes(s, s.dim) + mixed_real_work_bytes(s, s.real_warps);
     return ImageSmem<double>::bytes(s, s.dim) + real_work_bytes(s, precision, kRealWarps);
 }
 

@@ -87,6 +87,7 @@ struct SysDev {
     int n_lists, cand_pairs;
     int q_uniform;  // every mobile charge equal and every fixed charge equal
     int tile, n_mob_tiles, n_items;  // pair tiles (T = tile) and items per walker
+    int real_warps;                  // mixed form: warps per real-space CTA (8 or 16)
     const int2 *items;               // (ti, tj); tj >= n_mob_tiles -> fixed tile tj - n_mob_tiles
     // reciprocal space
     int n_runs, run_len, n_gh, n_gchunks, sfac_te;

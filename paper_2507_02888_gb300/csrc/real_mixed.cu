@@ -16,9 +16,9 @@ __global__ void __launch_bounds__(kRealMixedThreads, kRealMinBlocksMixed) k_real
     const long long total = (long long)b.W * s.n_items;
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
         const int w = (int)(item / s.n_items), p = (int)(item - (long long)w * s.n_items);
-        // units of 32 x 8 pairs: a 256 x 256 item splits evenly over the
-        // CTA's 16 warps (diagonal items: 144 units, the others 256)
-        real_item_mixed_cm<DIM, CM, QW>(s, b, w, p, ims, work, 4);
+        // units of 32 x 8 pairs (16 warps) or 32 x 16 (8 warps): a 256 x 256
+        // item splits evenly over the CTA's warps
+        real_item_mixed_cm<DIM, CM, QW>(s, b, w, p, ims, work, s.real_warps / 4);
     }
 }
 
@@ -44,12 +44,12 @@ static RealFn real_mixed_fn(const SysDev &s) {
 int configure_real_mixed(const SysDev &s, size_t smem, int *blocks_per_sm) {
     const RealFn f = real_mixed_fn(s);
     cudaError_t e = allow_max_smem(f, smem);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kRealMixedThreads, smem);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, 32 * s.real_warps, smem);
     return e;
 }
 
 int launch_real_mixed(const SysDev &s, const BatchDev &b, int grid, size_t smem, cudaStream_t st) {
-    real_mixed_fn(s)<<<grid, kRealMixedThreads, smem, st>>>(s, b);
+    real_mixed_fn(s)<<<grid, 32 * s.real_warps, smem, st>>>(s, b);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ class Desc(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("pair_tile", _c_int), ("subcell_bits", _c_int), ("ms", _c_double), ("n_tried", _c_int),
-                ("from_cache", _c_int)]
+                ("from_cache", _c_int), ("real_threads", _c_int), ("sfac_chunks", _c_int), ("sfac_ms", _c_double)]
 
 
 class Info(ctypes.Structure):
