@@ -59,8 +59,9 @@ def parse():
     p.add_argument("--no-jastrow", action="store_true", help="skip the two-body plane-wave Jastrow term")
     p.add_argument("--no-tune-alpha", action="store_true", help="skip the measured alpha balancing leg")
     p.add_argument("--serve-requests", type=int, default=2000)
-    p.add_argument("--serve-requests-fp64", type=int, default=120)
-    p.add_argument("--serve-requests-tiered", type=int, default=600)
+    p.add_argument("--serve-requests-fp64", type=int, default=120,
+                   help="plain-FP64 serving leg (2000 takes ~6 min: run it on request)")
+    p.add_argument("--serve-requests-tiered", type=int, default=2000)
     return p.parse_args()
 
 
@@ -801,8 +802,10 @@ def run_serving(stream, precision, n_requests, seed=4242):
     lam = 0.8 * sat_rate
     res = serve.run_stream(srv, make(n_requests, lam))
     srv.close()
+    lat = np.asarray(res["latency_ms"])
     return {"moves_per_s": res["moves"] / res["elapsed_s"], "unit": "walker moves/s (propose+accept)",
             "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"], "requests": n_requests,
+            "latencies_above_p99": int(np.sum(lat > res["p99_ms"])),
             "arrival_rate_per_s": lam, "saturated_moves_per_s": sat["moves"] / sat["elapsed_s"],
             "saturated_requests_per_s": sat_rate, "elapsed_s": res["elapsed_s"]}
 

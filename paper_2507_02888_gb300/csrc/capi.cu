@@ -8,6 +8,7 @@
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <set>
 #include <sstream>
 #include <new>
 #include <string>
@@ -114,6 +115,8 @@ int apply_tiling(ewald_ctx *c, int S, int bits) {
     if ((e = (cudaError_t)configure_launch(s, t.precision, &c->cfg))) return cuda_fail(c, e);
     return EWALD_OK;
 }
+
+size_t mixed_table_bytes(const HostTables &t0, int bits);
 
 // A tuned configuration: real-space tiling, the mixed form's CTA warps
 // (warps > 0) and the structure-factor chunks (chunks > 0).
@@ -267,14 +270,21 @@ int build_device(ewald_ctx *c) {
     // pair tiles of 32 x S particles per side; the largest item count (S = 1)
     // sizes the batches' partial-sum buffers, so any tiling fits later
     int S = t.n_mob >= 128 ? 4 : (t.n_mob >= 64 ? 2 : 1);
-    // the mixed form's pair loop takes 256-particle tiles (8 warps, no limit
-    // on the units of an item): a quarter of the item boundaries
-    if (t.precision == EWALD_MIXED && t.n_mob >= 256) S = 8;
+    int bits = t.sub_bits;
+    if (t.precision == EWALD_MIXED) {
+        // the mixed form's pair loop takes 256-particle tiles (no limit on
+        // the units of an item: a quarter of the item boundaries) where they
+        // pad the pairs no more than 128-particle tiles do
+        auto padded = [&](int T) { return std::ceil(t.n_mob / (double)T) * T; };
+        if (t.n_mob >= 256 && padded(256) <= padded(128)) S = 8;
+        // and candidate tables that leave room for its CTAs
+        while (bits > t.min_bits && mixed_table_bytes(t, bits) > kMixedTableBytes) --bits;
+    }
     {
         int nt1 = (t.n_mob + 31) / 32, nf1 = (t.n_fix + 31) / 32;
         c->max_items = nt1 * (nt1 + 1) / 2 + nt1 * nf1;
     }
-    return apply_tiling(c, S, t.sub_bits);
+    return apply_tiling(c, S, bits);
 }
 
 // The structure factor of a context's batch: the tiered FP64 form takes the
@@ -480,6 +490,19 @@ bool write_tune_cache(const char *path, const std::map<std::string, TuneEntry> &
     return std::rename(tmp.c_str(), path) == 0;
 }
 
+// Shared memory of the mixed loop's candidate tables for 2^bits cells per
+// axis: the distinct candidate lists as pairs of FP32 images.
+size_t mixed_table_bytes(const HostTables &t0, int bits) {
+    HostTables t = t0;
+    if (bits != t.sub_bits || t.cand.empty()) set_subcells(&t, bits);
+    const int np = mixed_pairs(t.cand_max), n_sub = (int)(t.cand.size() / std::max(t.cand_max, 1));
+    std::set<std::vector<unsigned short>> lists;
+    for (int r = 0; r < n_sub; ++r)
+        lists.insert(std::vector<unsigned short>(t.cand.begin() + (size_t)r * t.cand_max,
+                                                 t.cand.begin() + (size_t)(r + 1) * t.cand_max));
+    return lists.size() * np * (t.dim == 3 ? sizeof(float4) + sizeof(float2) : sizeof(float4));
+}
+
 bool tiling_allowed(const ewald_ctx *c, int S, int bits) {
     const HostTables &t = c->t;
     if (32 * S > std::max(32, 2 * t.n_mob)) return false;
@@ -487,7 +510,8 @@ bool tiling_allowed(const ewald_ctx *c, int S, int bits) {
     // loops sum at most 16 sub-tile units per item)
     if (S > 4 && (t.precision != EWALD_MIXED || S != 8)) return false;
     int max_bits = t.dim == 3 ? 4 : 6;
-    return bits >= t.min_bits && bits <= max_bits && subcell_bytes(t, bits) <= 48 * 1024;
+    if (bits < t.min_bits || bits > max_bits || subcell_bytes(t, bits) > 48 * 1024) return false;
+    return t.precision != EWALD_MIXED || mixed_table_bytes(t, bits) <= kMixedTableBytes;
 }
 
 bool ready(ewald_batch *b) {

@@ -32,6 +32,9 @@ constexpr int kRealMinBlocks32 = 11, kRealMinBlocks64 = 8;
 // the mixed path's real-space kernel: warps per CTA (sharing one copy of the
 // candidate tables) and resident CTAs per SM its registers are sized for
 constexpr int kRealMixedWarps = 16, kRealMixedThreads = 32 * kRealMixedWarps, kRealMinBlocksMixed = 2;
+// largest shared-memory footprint of the mixed loop's candidate tables
+// chosen by default or by the autotuner
+constexpr size_t kMixedTableBytes = 24 * 1024;
 // per-warp queues of accepted (r^2, weight) terms: the FP32 one a ring
 // flushed 64 entries at a time, the FP64 one flushed 32 at a time
 constexpr int kQueueCap32 = 128, kQueueCap64 = 96;
