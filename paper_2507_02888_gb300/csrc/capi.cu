@@ -74,6 +74,7 @@ int apply_tiling(ewald_ctx *c, int S, int bits) {
     if ((e = upload(c->dev, (unsigned short **)&s.cand, t.cand.data(), t.cand.size()))) return cuda_fail(c, e);
     {   // the mixed loop's tables: distinct lists as pairs of FP32 images
         const int np = mixed_pairs(t.cand_max), n_sub = (int)(t.cand.size() / std::max(t.cand_max, 1));
+        const int pstride = np | 1;  // odd: consecutive lists start in different banks
         std::map<std::vector<unsigned short>, int> ids;
         std::vector<unsigned short> clist(n_sub);
         std::vector<float4> cxy;
@@ -87,8 +88,8 @@ int apply_tiling(ewald_ctx *c, int S, int bits) {
             auto it = ids.find(l);
             if (it == ids.end()) {
                 it = ids.emplace(l, (int)ids.size()).first;
-                for (int p = 0; p < np; ++p) {
-                    const int a = l[2 * p], b = l[2 * p + 1];
+                for (int p = 0; p < pstride; ++p) {  // pairs past np: padding between lists
+                    const int a = p < np ? l[2 * p] : s.n_img, b = p < np ? l[2 * p + 1] : s.n_img;
                     cxy.push_back(make_float4(imf(a, 0), imf(b, 0), imf(a, 1), imf(b, 1)));
                     cz.push_back(make_float2(t.dim == 3 ? imf(a, 2) : 0.0f, t.dim == 3 ? imf(b, 2) : 0.0f));
                 }
@@ -98,6 +99,7 @@ int apply_tiling(ewald_ctx *c, int S, int bits) {
         if (ids.size() > 65535) return fail(c, EWALD_ERR_ARG, "too many distinct candidate lists");
         s.n_lists = (int)ids.size();
         s.cand_pairs = np;
+        s.cand_pstride = pstride;
         if ((e = upload(c->dev, (float4 **)&s.cxy, cxy.data(), cxy.size()))) return cuda_fail(c, e);
         if ((e = upload(c->dev, (float2 **)&s.cz, cz.data(), cz.size()))) return cuda_fail(c, e);
         if ((e = upload(c->dev, (unsigned short **)&s.clist, clist.data(), clist.size()))) return cuda_fail(c, e);
@@ -279,6 +281,9 @@ int build_device(ewald_ctx *c) {
         if (t.n_mob >= 256 && padded(256) <= padded(128)) S = 8;
         // and candidate tables that leave room for its CTAs
         while (bits > t.min_bits && mixed_table_bytes(t, bits) > kMixedTableBytes) --bits;
+        // CTAs of 16 warps for 256-particle tiles, 8 for smaller ones (an item
+        // then still gives every warp several units)
+        s.real_warps = S == 8 ? 16 : 8;
     }
     {
         int nt1 = (t.n_mob + 31) / 32, nf1 = (t.n_fix + 31) / 32;
@@ -500,7 +505,7 @@ size_t mixed_table_bytes(const HostTables &t0, int bits) {
     for (int r = 0; r < n_sub; ++r)
         lists.insert(std::vector<unsigned short>(t.cand.begin() + (size_t)r * t.cand_max,
                                                  t.cand.begin() + (size_t)(r + 1) * t.cand_max));
-    return lists.size() * np * (t.dim == 3 ? sizeof(float4) + sizeof(float2) : sizeof(float4));
+    return lists.size() * (np | 1) * (t.dim == 3 ? sizeof(float4) + sizeof(float2) : sizeof(float4));
 }
 
 bool tiling_allowed(const ewald_ctx *c, int S, int bits) {

@@ -88,6 +88,8 @@ struct SysDev {
     const float2 *cz;
     const unsigned short *clist;
     int n_lists, cand_pairs;
+    int cand_pstride;  // pairs from one list to the next: odd, so that lanes reading pair p of
+                       // different lists fall in different banks of shared memory
     int q_uniform;  // every mobile charge equal and every fixed charge equal
     int tile, n_mob_tiles, n_items;  // pair tiles (T = tile) and items per walker
     int real_warps;                  // mixed form: warps per real-space CTA (8 or 16)

@@ -46,24 +46,25 @@ struct __align__(16) Tile16 {
 // cells share a list), as pairs of images in the operand layout of the
 // paired FP32 instructions: for pair p of list L, xy[L][p] = (X_a, X_b,
 // Y_a, Y_b) and, in 3D, z[L][p] = (Z_a, Z_b) (lists padded with the far
-// sentinel to cand_pairs pairs); clist[cell] is the cell's list.
+// sentinel to cand_pairs pairs, stored cand_pstride pairs apart); clist[cell]
+// is the cell's list.
 struct MixedImageSmem {
     float4 *xy;
     float2 *z;
     unsigned short *clist;
     __host__ __device__ static size_t bytes(const SysDev &s, int dim) {
-        const size_t n_sub = (size_t)1 << (s.sub_bits * dim), np = (size_t)s.n_lists * s.cand_pairs;
+        const size_t n_sub = (size_t)1 << (s.sub_bits * dim), np = (size_t)s.n_lists * s.cand_pstride;
         return align16(np * sizeof(float4)) + (dim == 3 ? align16(np * sizeof(float2)) : 0) +
                align16(n_sub * sizeof(unsigned short));
     }
     __device__ void carve(unsigned char *base, const SysDev &s, int dim) {
-        const size_t np = (size_t)s.n_lists * s.cand_pairs;
+        const size_t np = (size_t)s.n_lists * s.cand_pstride;
         xy = (float4 *)base;
         z = (float2 *)(base + align16(np * sizeof(float4)));
         clist = (unsigned short *)(base + align16(np * sizeof(float4)) + (dim == 3 ? align16(np * sizeof(float2)) : 0));
     }
     __device__ void stage(const SysDev &s, int dim) {
-        const int n_sub = 1 << (s.sub_bits * dim), np = s.n_lists * s.cand_pairs;
+        const int n_sub = 1 << (s.sub_bits * dim), np = s.n_lists * s.cand_pstride;
         for (int i = threadIdx.x; i < np; i += blockDim.x) xy[i] = s.cxy[i];
         if (dim == 3)
             for (int i = threadIdx.x; i < np; i += blockDim.x) z[i] = s.cz[i];
@@ -167,6 +168,9 @@ struct LaneRing {
     // let the lanes with two waiting evaluate until it can
     template <int ROOM>
     __device__ void service(Acc<float> &acc, const TermK32 &tk) {
+        // a lane above the threshold has at least two entries, so every
+        // forced evaluation below shortens the longest ring: the loop ends
+        static_assert(CAP - ROOM >= 2, "ring too short for the entries pushed between services");
         const unsigned pend = cnt - hd;
         const unsigned lo = __reduce_min_sync(0xffffffffu, pend);
         for (unsigned n = lo >> 1; n > 0; --n) eval_two(acc, tk);
@@ -260,17 +264,27 @@ __device__ __forceinline__ void test_pairs(const float4 *xy, const float2 *zz, c
 
 // Candidate slots with a compiled pair loop (pairs of images); a list of
 // another length runs the next longer one (padded with the sentinel),
-// longer than 8 the chunked loop (slots = 0: chunks of 4 pairs).
+// longer than 8 the chunked loop (slots = 0: chunks of 8 pairs).
 __host__ __device__ inline int mixed_cm(int cand_max) {
     return cand_max <= 2 ? 2 : cand_max <= 4 ? 4 : cand_max <= 6 ? 6 : cand_max <= 8 ? 8 : 0;
 }
 __host__ __device__ inline int mixed_pairs(int cand_max) {
     const int cm = mixed_cm(cand_max);
-    return cm ? cm / 2 : (cand_max + 7) / 8 * 4;
+    return cm ? cm / 2 : (cand_max + 15) / 16 * 8;
 }
+// pairs of images per chunk of a long list: 8, or 4 for rings too short to
+// take 16 entries between services
+template <int CAP>
+constexpr int kChunkPairs = CAP >= 32 ? 8 : 4;
+// Particle pairs between services of the rings: short lists are serviced
+// every few pairs (PAIRS_PER_SERVICE x CM entries at most come in between)
+template <int CM>
+constexpr int kPairsPerService = CM == 2 ? 4 : CM == 4 ? 2 : 1;
 
 // The images of one pair of particles: CM candidate slots (CM = 2 ... 8
-// compile-time; CM = 0: the list in chunks of 4 pairs)
+// compile-time; the caller services the rings every kPairsPerService<CM>
+// pairs) or, CM = 0, the list in chunks of 8 pairs (serviced here after
+// every chunk but the last, which the caller's service follows)
 template <int DIM, int CM, bool QW, int CAP>
 __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem &ims, const Tile16 &a,
                                           const Tile16 &b, bool valid, float wgt, LaneRing<QW, CAP> &ring,
@@ -278,21 +292,27 @@ __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem 
     float x[DIM], z2;
     const int sc = pair_cart<DIM>(s, a, b, x, z2);
     const float rc2 = valid ? s.rc2_f : 0.0f;  // invalid lanes never pass
-    const int base = ims.clist[sc] * s.cand_pairs;
+    const int base = ims.clist[sc] * s.cand_pstride;
     const float4 *xy = ims.xy + base;
     const float2 *zz = ims.z + base;
     if (CM > 0) {
         test_pairs<DIM, CM / 2, true, QW, CAP>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
-        ring.template service<CM>(acc, tk);
     } else {
-        test_pairs<DIM, 4, true, QW, CAP>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
-        ring.template service<8>(acc, tk);
-        for (int ch = 4; ch < s.cand_pairs; ch += 4) {
+        constexpr int CP = kChunkPairs<CAP>;
+        test_pairs<DIM, CP, true, QW, CAP>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
+        for (int ch = CP; ch < s.cand_pairs; ch += CP) {
+            ring.template service<2 * CP>(acc, tk);
             bool unused;
-            test_pairs<DIM, 4, false, QW, CAP>(xy + ch, zz + ch, x, z2, rc2, s.close2_f, wgt, ring, unused);
-            ring.template service<8>(acc, tk);
+            test_pairs<DIM, CP, false, QW, CAP>(xy + ch, zz + ch, x, z2, rc2, s.close2_f, wgt, ring, unused);
         }
     }
+}
+
+// The rings' service after the pairs of a step (see kPairsPerService)
+template <int CM, bool QW, int CAP>
+__device__ __forceinline__ void ring_service(LaneRing<QW, CAP> &ring, Acc<float> &acc, const TermK32 &tk) {
+    constexpr int room = CM > 0 ? CM * kPairsPerService<CM> : 2 * kChunkPairs<CAP>;
+    ring.template service<room>(acc, tk);
 }
 
 // One (walker w, tile pair p) item: E_real partial sum of the item into
@@ -366,6 +386,8 @@ __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, in
             const float wgt = QW ? pi.q * pj.q : 1.0f;
             bool close = false;
             pair_ring<DIM, CM, QW, kLaneRing>(s, ims, pi, pj, valid, wgt, ring, close, acc, tk);
+            if ((jj - j_lo) % kPairsPerService<CM> == kPairsPerService<CM> - 1 || jj + 1 == j_end)
+                ring_service<CM>(ring, acc, tk);
             const unsigned cb = __ballot_sync(0xffffffffu, close);
             if (cb) {  // uniform over the warp, rare
                 const int at = cl.n + __popc(cb & ((1u << lane) - 1u));
