@@ -549,6 +549,7 @@ const char *ewald_strerror(int code) {
 }
 
 int ewald_create(const ewald_desc *desc, void *cuda_stream, ewald_ctx **out) {
+    EWALD_NVTX("ewald_create");
     if (!out) return EWALD_ERR_ARG;
     *out = nullptr;
     ewald_ctx *c = new (std::nothrow) ewald_ctx();
@@ -652,6 +653,7 @@ int ewald_last_error(const ewald_ctx *c) {
 }
 
 int ewald_batch_create(ewald_ctx *c, int W, ewald_batch **out) {
+    EWALD_NVTX("ewald_batch_create");
     if (!out) return fail(c, EWALD_ERR_ARG);
     *out = nullptr;
     if (!c || W < 1) return fail(c, EWALD_ERR_ARG, "need a context and W >= 1");
@@ -720,6 +722,7 @@ void ewald_batch_destroy(ewald_batch *b) {
 }
 
 int ewald_batch_set_positions(ewald_batch *b, const double *pos, int on_device) {
+    EWALD_NVTX("ewald_batch_set_positions");
     if (!b || !pos) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     ewald_ctx *c = b->ctx;
     const double *src = pos;
@@ -739,6 +742,7 @@ int ewald_batch_set_positions(ewald_batch *b, const double *pos, int on_device) 
 }
 
 int ewald_batch_get_positions(ewald_batch *b, double *pos, int on_device) {
+    EWALD_NVTX("ewald_batch_get_positions");
     if (!ready(b) || !pos) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     ewald_ctx *c = b->ctx;
     size_t n = (size_t)b->b.W * c->s.n_mob * c->s.dim * sizeof(double);
@@ -755,6 +759,7 @@ int ewald_batch_sync(ewald_batch *b) {
 }
 
 int ewald_energy(ewald_batch *b, double *e_out, int on_device) {
+    EWALD_NVTX("ewald_energy");
     if (!ready(b) || !e_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     int e = run_energy(b);
     if (e) return e;
@@ -763,6 +768,7 @@ int ewald_energy(ewald_batch *b, double *e_out, int on_device) {
 }
 
 int ewald_energy_components(ewald_batch *b, double *comp_out, int on_device) {
+    EWALD_NVTX("ewald_energy_components");
     if (!ready(b) || !comp_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     int e = run_energy(b);
     if (e) return e;
@@ -771,6 +777,7 @@ int ewald_energy_components(ewald_batch *b, double *comp_out, int on_device) {
 }
 
 int ewald_propose_move(ewald_batch *b, const int *k, const double *r_new, double *de_out, int on_device) {
+    EWALD_NVTX("ewald_propose_move");
     if (!ready(b) || !k || !r_new || !de_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     ewald_ctx *c = b->ctx;
     const int W = b->b.W, dim = c->s.dim;
@@ -806,6 +813,7 @@ int ewald_propose_move(ewald_batch *b, const int *k, const double *r_new, double
 }
 
 int ewald_accept_move(ewald_batch *b, const unsigned char *accept, int on_device) {
+    EWALD_NVTX("ewald_accept_move");
     if (!ready(b) || !accept) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     ewald_ctx *c = b->ctx;
     if (!b->has_pending) return fail(c, EWALD_ERR_NO_PROPOSAL, "no pending proposal");
@@ -830,12 +838,14 @@ int ewald_accept_move(ewald_batch *b, const unsigned char *accept, int on_device
 }
 
 int ewald_resum(ewald_batch *b) {
+    EWALD_NVTX("ewald_resum");
     if (!ready(b)) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     b->rho_stale = true;
     return ensure_rho(b);
 }
 
 int ewald_batch_get_rho(ewald_batch *b, double *rho_out, int on_device) {
+    EWALD_NVTX("ewald_batch_get_rho");
     if (!ready(b) || !rho_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     ewald_ctx *c = b->ctx;
     if (int r = ensure_rho(b)) return r;
@@ -898,6 +908,7 @@ double item_cost(const SysDev &s, int kind, int sub) {
 }  // namespace
 
 int ewald_multi_create(ewald_batch *const *batches, int n, ewald_multi **out) {
+    EWALD_NVTX("ewald_multi_create");
     if (!out) return EWALD_ERR_ARG;
     *out = nullptr;
     if (!batches || n < 1) return EWALD_ERR_ARG;
@@ -1067,6 +1078,7 @@ void ewald_multi_destroy(ewald_multi *m) {
 }
 
 int ewald_multi_energy(ewald_multi *m, double *e_out, int on_device) {
+    EWALD_NVTX("ewald_multi_energy");
     if (!m || !e_out) return EWALD_ERR_ARG;
     cudaError_t e = cudaSuccess;
     // the batches' own streams first finish what they have queued
@@ -1097,6 +1109,7 @@ int ewald_multi_energy(ewald_multi *m, double *e_out, int on_device) {
 }
 
 int ewald_autotune(ewald_batch *b, const char *cache_path, ewald_tune_result *res) {
+    EWALD_NVTX("ewald_autotune");
     if (!b || !b->ctx) return EWALD_ERR_ARG;
     if (!b->has_pos) return fail(b->ctx, EWALD_ERR_STATE, "positions not set");
     ewald_ctx *c = b->ctx;

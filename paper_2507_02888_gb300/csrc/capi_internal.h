@@ -5,6 +5,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "device_common.cuh"
 
 struct ewald_ctx {
@@ -59,6 +61,17 @@ struct ewald_batch {
 };
 
 namespace ewald_capi {
+
+// An NVTX range over an entry point (named "ewald_energy" and so on), so that
+// a profiler's timeline shows each library call around the kernels it
+// launched.  Without a tool attached a range costs a few instructions.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define EWALD_NVTX(name) ewald_capi::NvtxRange ewald_nvtx_range_(name)
 
 inline int fail(ewald_ctx *c, int code, const char *why = nullptr) {
     if (c && code) {

@@ -244,6 +244,7 @@ int ewald_jastrow_p_set(ewald_ctx *c, int n_stars, const double *a) {
 }
 
 int ewald_jastrow_p(ewald_batch *b, double *j_out, double *grad_out, double *lap_out, int on_device) {
+    EWALD_NVTX("ewald_jastrow_p");
     if (!b || !b->ctx || !j_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     ewald_ctx *c = b->ctx;
     if (!b->has_pos) return fail(c, EWALD_ERR_STATE, "positions not set");

@@ -389,6 +389,7 @@ int ewald_jastrow_u_set(ewald_ctx *c, int n_up, double L_u, int C, int n_u, cons
 }
 
 int ewald_jastrow_u(ewald_batch *b, double *j_out, double *grad_out, double *lap_out, int on_device) {
+    EWALD_NVTX("ewald_jastrow_u");
     if (!b || !b->ctx || !j_out) return fail(b ? b->ctx : nullptr, EWALD_ERR_ARG);
     ewald_ctx *c = b->ctx;
     if (!b->has_pos) return fail(c, EWALD_ERR_STATE, "positions not set");

@@ -105,6 +105,7 @@ static size_t noalloc_walker_limit(const SysDev &s) {
 
 extern "C" int ewald_energy_noalloc(ewald_ctx *c, const double *pos, int n_walkers, double *e_out,
                                     int *status_out) {
+    EWALD_NVTX("ewald_energy_noalloc");
     using namespace ewald_capi;
     if (!c) return EWALD_ERR_ARG;
     if (!pos || !e_out || n_walkers < 1)

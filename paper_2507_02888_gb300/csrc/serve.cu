@@ -328,6 +328,7 @@ const char *ewald_server_error_message(const ewald_server *s) { return s ? s->wh
 
 int ewald_server_submit(ewald_server *s, ewald_ctx *system, const double *pos, int n_walkers, int n_steps,
                         double sigma, double accept_prob, unsigned long long seed, int *request_id) {
+    EWALD_NVTX("ewald_server_submit");
     if (!s || !system || !pos || !request_id || n_walkers < 1 || n_steps < 0 || !(sigma >= 0) ||
         !(accept_prob >= 0 && accept_prob <= 1))
         return srv_fail(s, EWALD_ERR_ARG, "bad request");
@@ -358,6 +359,7 @@ int ewald_server_submit(ewald_server *s, ewald_ctx *system, const double *pos, i
 }
 
 int ewald_server_step(ewald_server *s, int *n_active, int *n_queued) {
+    EWALD_NVTX("ewald_server_step");
     if (!s) return EWALD_ERR_ARG;
     cudaError_t e;
     // 1. requests whose results have arrived

@@ -50,6 +50,7 @@ double time_alpha(const ewald_desc &base, double alpha, void *stream, int W, con
 
 extern "C" int ewald_tune_alpha(const ewald_desc *desc, void *cuda_stream, int n_walkers, const double *pos,
                                 double *alpha_out, double *us_per_walker) {
+    EWALD_NVTX("ewald_tune_alpha");
     if (!desc || !pos || !alpha_out || n_walkers < 1) return EWALD_ERR_ARG;
     if (desc->r_cutoff > 0 || desc->g_cutoff > 0) return EWALD_ERR_ARG;  // cutoffs follow alpha
     // starting point: the desc's alpha, else the library's balanced default
