@@ -131,6 +131,14 @@ int ewald_get_gvectors(const ewald_ctx *ctx, int *nvec);
  * that checks it). */
 int ewald_last_error(const ewald_ctx *ctx);
 const char *ewald_strerror(int code);
+/* How the library was built: EWALD_BUILD_DEBUG_CHECKS set for the debug
+ * build (libewald_gb300_debug.so, compiled with -DEWALD_DEBUG), whose
+ * kernels check their ring and queue fill levels, candidate-list, G-slot
+ * and particle indices, skip an out-of-range access and report it as
+ * EWALD_ERR_STATE on the next synchronising call.  Not in the paper: a
+ * development aid, for tiny cases compared with the ordinary build. */
+#define EWALD_BUILD_DEBUG_CHECKS 1
+int ewald_build_flags(void);
 /* A one-line description of the context's last failure (argument checked,
  * CUDA call and its error string, ...); valid until the next call on the
  * context.  Never NULL. */

@@ -351,6 +351,11 @@ int sync_status(ewald_batch *b) {
     int st = *h;
     if (!st) return EWALD_OK;
     if ((e = cudaMemsetAsync(b->b.status, 0, sizeof(int), c->stream))) return cuda_fail(c, e);
+    if (st & ST_DEBUG_RANGE) {
+        c->why = "debug build: a kernel caught an index out of range (check at source line " +
+                 std::to_string((st >> 8) & 0xffff) + ")";
+        return fail(c, EWALD_ERR_STATE);
+    }
     if (st & ST_COINCIDENT) return fail(c, EWALD_ERR_COINCIDENT, "coincident particles");
     if (st & ST_TIMEOUT) return fail(c, EWALD_ERR_TIMEOUT, "device wait timed out");
     return fail(c, EWALD_ERR_ARG, st & ST_BAD_INDEX ? "move index or position invalid" : "non-finite position");
@@ -531,6 +536,14 @@ bool ready(ewald_batch *b) {
 }  // namespace
 
 extern "C" {
+
+int ewald_build_flags(void) {
+#ifdef EWALD_DEBUG
+    return EWALD_BUILD_DEBUG_CHECKS;
+#else
+    return 0;
+#endif
+}
 
 const char *ewald_strerror(int code) {
     switch (code) {

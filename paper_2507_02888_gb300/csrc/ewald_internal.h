@@ -60,7 +60,26 @@ struct __align__(32) Img64 {
 };
 
 // Device-side error bits, OR-ed into the batch status word by kernels.
-enum : int { ST_COINCIDENT = 1, ST_BAD_INDEX = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
+enum : int { ST_COINCIDENT = 1, ST_BAD_INDEX = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8, ST_DEBUG_RANGE = 16 };
+
+// Index checks of the debug build (compiled with -DEWALD_DEBUG): where
+// EWALD_IN_RANGE(cond, status) is false the kernel ORs ST_DEBUG_RANGE into
+// the status word, records the check's source line in bits 8-23 (the first
+// miss that gets there), and skips the access (the call then reports
+// EWALD_ERR_STATE with that line); in the ordinary build the check compiles
+// to nothing.
+#ifdef EWALD_DEBUG
+#ifdef __CUDACC__
+__device__ inline bool ewald_debug_miss(int *status, int line) {
+    const int old = atomicOr(status, ST_DEBUG_RANGE) | ST_DEBUG_RANGE;
+    if (!(old >> 8)) atomicCAS(status, old, old | ((line & 0xffff) << 8));  // one try: a clash keeps the first
+    return false;
+}
+#endif
+#define EWALD_IN_RANGE(cond, status) ((cond) ? true : ewald_debug_miss((status), __LINE__))
+#else
+#define EWALD_IN_RANGE(cond, status) true
+#endif
 
 // Per-system constants and table pointers; passed by value to kernels.
 struct SysDev {

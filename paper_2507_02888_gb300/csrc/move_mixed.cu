@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kProposeMixedThreads)
         const unsigned u2o = DIM == 2 ? (layered ? __float_as_uint(zk) : 0u) : uo[2];
         const unsigned u2n = DIM == 2 ? (layered ? __float_as_uint(zk) : 0u) : un[2];
         // real space: slot t = (other particle jj, old/new) over the CTA's lanes
-        LaneRing<true, kMoveRing> ring{m.rings + (size_t)warp * kMoveRing * 32 * 2 + lane, 0u, 0u};
+        LaneRing<true, kMoveRing> ring{m.rings + (size_t)warp * kMoveRing * 32 * 2 + lane, 0u, 0u, b.status};
         Acc<float> acc;
         double acc64 = 0.0;
         // slot t: the other particle of index jj (mobile ones except k, then
@@ -140,7 +140,9 @@ __global__ void __launch_bounds__(kProposeMixedThreads)
             fixedj = jj >= s.n_mob - 1;
             j = fixedj ? jj - (s.n_mob - 1) : (jj < k ? jj : jj + 1);
             Tile16 p = {{0u, 0u, 0u}, 0.0f};
-            if (t < 2 * n_other) p = fixedj ? tile16_fixed<DIM>(s, j) : tile16_mobile<DIM>(s, b, w, j);
+            if (t < 2 * n_other &&
+                EWALD_IN_RANGE(j >= 0 && (fixedj ? j < s.n_fix : j < s.n_mob && j != k), b.status))
+                p = fixedj ? tile16_fixed<DIM>(s, j) : tile16_mobile<DIM>(s, b, w, j);
             return p;
         };
         int jn;

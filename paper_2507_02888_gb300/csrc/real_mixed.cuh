@@ -134,10 +134,11 @@ template <bool QW, int CAP = kLaneRing>
 struct LaneRing {
     float *col;      // this lane's column
     unsigned cnt, hd;
+    int *status = nullptr;  // the batch's status word (checks of the debug build)
     __device__ float *at(unsigned k) const { return col + (k & (CAP - 1)) * 32; }
     __device__ void push(bool pass, float r2, float wgt) {
         float *e = at(cnt);
-        if (pass) {
+        if (pass && EWALD_IN_RANGE(cnt - hd < (unsigned)CAP, status)) {  // an entry not yet evaluated
             e[0] = r2;
             if (QW) e[CAP * 32] = wgt;
         }
@@ -292,7 +293,9 @@ __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem 
     float x[DIM], z2;
     const int sc = pair_cart<DIM>(s, a, b, x, z2);
     const float rc2 = valid ? s.rc2_f : 0.0f;  // invalid lanes never pass
-    const int base = ims.clist[sc] * s.cand_pstride;
+    const int sub = EWALD_IN_RANGE(sc < (1 << (s.sub_bits * DIM)), ring.status) ? sc : 0;
+    const int lid = ims.clist[sub];
+    const int base = (EWALD_IN_RANGE(lid < s.n_lists, ring.status) ? lid : 0) * s.cand_pstride;
     const float4 *xy = ims.xy + base;
     const float2 *zz = ims.z + base;
     if (CM > 0) {
@@ -351,7 +354,7 @@ __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, in
     const TermK32 tk = FP<float>::term_consts(s);
     // the item's common weight (charges all equal within each kind)
     const float wq = QW ? 1.0f : s.q_mob_f[0] * (fixedj ? s.q_fix_f[0] : s.q_mob_f[0]);
-    LaneRing<QW> ring{rings + (size_t)warp * kLaneRing * 32 * (QW ? 2 : 1) + lane, 0u, 0u};
+    LaneRing<QW> ring{rings + (size_t)warp * kLaneRing * 32 * (QW ? 2 : 1) + lane, 0u, 0u, b.status};
     Acc<float> acc;       // FP32 terms (weighted if QW)
     double acc64 = 0.0;   // close pairs in FP64, weighted
     const bool diag = !fixedj && tt.x == tt.y;

@@ -105,13 +105,16 @@ SIGNATURES = [
     ("ewald_jastrow_u_set", _c_int, [_vp, _c_int, _c_double, _c_int, _c_int, _vp, _vp]),
     ("ewald_jastrow_u", _c_int, [_vp, _vp, _vp, _vp, _c_int]),
     ("ewald_tune_alpha", _c_int, [_vp, _vp, _c_int, _vp, _vp, _vp]),
+    ("ewald_build_flags", _c_int, []),
 ]
 
 KERNELS = ["ingest", "sfac", "real", "combine", "propose", "accept", "resum"]
 
 
 def library_path():
-    return _build.LIB
+    """The release library, or the debug one (kernels check their indices)
+    when the environment sets EWALD_LIBRARY=debug."""
+    return _build.LIB_DEBUG if os.environ.get("EWALD_LIBRARY") == "debug" else _build.LIB
 
 
 def load(build_if_missing=True):
@@ -119,17 +122,23 @@ def load(build_if_missing=True):
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
-    if not os.path.exists(_build.LIB):
-        raise ImportError("libewald_gb300.so is not built; run python -m paper_2507_02888_gb300.build")
-    lib = ctypes.CDLL(_build.LIB)
+    path = library_path()
+    if build_if_missing and not _build.up_to_date(path):
+        _build.build_variants(("debug",) if path == _build.LIB_DEBUG else ("release",))
+    if not os.path.exists(path):
+        raise ImportError("%s is not built; run python -m paper_2507_02888_gb300.build" % os.path.basename(path))
+    lib = ctypes.CDLL(path)
     for name, res, args in SIGNATURES:
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def build_flags():
+    """EWALD_BUILD_* bits of the loaded library (1: the debug build)."""
+    return int(load().ewald_build_flags())
 
 
 def _check(code, ctx=None):
