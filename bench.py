@@ -188,6 +188,16 @@ REAL_SOURCES = ["paper_2507_02888_gb300/csrc/real_mixed.cu", "paper_2507_02888_g
                 "paper_2507_02888_gb300/csrc/ewald_internal.h", "paper_2507_02888_gb300/csrc/device_common.cuh"]
 
 
+def real_kernel_name(info, w):
+    """The k_real_mixed instantiation the library launches for this system:
+    candidate slots rounded up to 2, 4, 6 or 8 (0: longer lists, walked in
+    chunks), and whether the pair weights vary (the mobile or the fixed
+    charges not all equal in FP32)."""
+    cm = next((c for c in (2, 4, 6, 8) if info["max_candidates"] <= c), 0)
+    qw = int(any(len(q) and np.ptp(np.asarray(q, dtype=np.float32)) != 0 for q in (w["q"], w["fixed_q"])))
+    return "k_real_mixed<%d,%d,%d>" % (info["dim"], cm, qw)
+
+
 def profiled_traffic(workload, precision):
     """DRAM bytes per launch of the real-space kernel from the committed ncu summary, if current."""
     p = os.path.join(ROOT, "profiles", "real_%s_%s.json" % (precision, workload))
@@ -382,7 +392,7 @@ def run_ours(args, rank, world, local_rank):
                   "roofline": move_roofline(info, w, W, moves_per_s, float(np.mean(acc)), peaks, hbm_peak,
                                             hbm_basis)},
         "kernel_ms_per_launch": kernel_ms,
-        "roofline": {"bound": "alu", "kernel": "k_real<float,%d>" % dim, "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": real_kernel_name(info, w), "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal)",
                      "work": "%d flop per real-space term inside r_c, %.4g terms per launch"
