@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kProposeMixedThreads)
             const Tile16 pkw = which ? Tile16{{un[0], un[1], u2n}, qk} : Tile16{{uo[0], uo[1], u2o}, qk};
             bool close = false;
             pair_ring<DIM, CM, true, kMoveRing>(s, m.ims, pkw, pj, v, wgt, ring, close, acc, tk);
-            ring_service<CM>(ring, acc, tk);
+            ring_service<CM, 1>(ring, acc, tk);
             if (__any_sync(0xffffffffu, close) && close) {  // rare: the FP64 term now
                 float x[DIM], z2;
                 const int sc = pair_cart<DIM>(s, pkw, pj, x, z2);
