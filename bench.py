@@ -246,6 +246,7 @@ def de_stats(de, de_fp64, floor):
     rel = d / np.maximum(np.abs(de_fp64), 1e-300)
     return {"walkers": int(d.size), "abs_max_ha": float(np.max(d)), "abs_median_ha": float(np.median(d)),
             "vs_walker_floor_max": float(np.max(d / floor)),
+            "vs_abs_de_mean": float(np.mean(rel)),
             "vs_abs_de_median": float(np.median(rel)), "vs_abs_de_p99": float(np.percentile(rel, 99)),
             "vs_abs_de_max": float(np.max(rel)), "frac_within_1e-6_of_abs_de": float(np.mean(rel <= 1e-6)),
             "abs_de_median_ha": float(np.median(np.abs(de_fp64)))}

@@ -19,7 +19,11 @@
 
 namespace ewald {
 
-constexpr int kProposeMixedThreads = 256;
+// four warps per CTA: more walkers in flight per SM (7 CTAs at the fcc
+// workload's 31 KB of shared memory) hide the per-walker chain of
+// dependent steps better than wider CTAs (measured per round of 4096 fcc
+// walkers: 64 threads 0.207 ms, 96 0.182, 128 0.166, 256 0.176, 512 0.227)
+constexpr int kProposeMixedThreads = 128;
 // pending terms per lane: a walker's move gives each lane ~25 terms, so a
 // short ring (with weights: +-q_k q_j) keeps the CTA small
 constexpr int kMoveRing = 16;
