@@ -112,9 +112,12 @@ __global__ void __launch_bounds__(kMoveThreads)
 // thread's G run of rho(G) loaded before the recurrence updates it (the
 // loads of a run are independent, so up to kRunLen are in flight per
 // thread), the float-pair rho updated by two-sums, and walkers due for a
-// re-sum listed in b.resum_list.
+// re-sum listed in b.resum_list.  CTAs of four warps: each thread takes
+// about three runs, and more walkers are in flight per SM (measured per
+// round of 4096 fcc walkers: 64 threads 0.043 ms, 128 0.033, 256 0.044).
+constexpr int kAcceptMixedThreads = 128;
 template <int DIM>
-__global__ void __launch_bounds__(kMoveThreads)
+__global__ void __launch_bounds__(kAcceptMixedThreads)
     k_accept_mixed(SysDev s, BatchDev b, const unsigned char *__restrict__ acc, int resum_every) {
     extern __shared__ __align__(32) unsigned char smem[];
     MoveSmem<float> m;
@@ -224,8 +227,8 @@ int launch_accept(const SysDev &s, const BatchDev &b, int precision, const Launc
     if (precision != EWALD_FP64 && b.resum_list) {
         cudaError_t e = cudaMemsetAsync(b.resum_list, 0, sizeof(int), st);
         if (e) return e;
-        if (s.dim == 3) k_accept_mixed<3><<<b.W, kMoveThreads, cfg.move_smem, st>>>(s, b, acc, resum_every);
-        else k_accept_mixed<2><<<b.W, kMoveThreads, cfg.move_smem, st>>>(s, b, acc, resum_every);
+        if (s.dim == 3) k_accept_mixed<3><<<b.W, kAcceptMixedThreads, cfg.move_smem, st>>>(s, b, acc, resum_every);
+        else k_accept_mixed<2><<<b.W, kAcceptMixedThreads, cfg.move_smem, st>>>(s, b, acc, resum_every);
         return cudaGetLastError();
     }
     if (precision == EWALD_FP64) {
