@@ -78,7 +78,7 @@ __device__ inline bool ewald_debug_miss(int *status, int line) {
 #endif
 #define EWALD_IN_RANGE(cond, status) ((cond) ? true : ewald_debug_miss((status), __LINE__))
 #else
-#define EWALD_IN_RANGE(cond, status) true
+#define EWALD_IN_RANGE(cond, status) ((void)sizeof(cond), true)
 #endif
 
 // Per-system constants and table pointers; passed by value to kernels.

@@ -35,8 +35,23 @@ def test_library_exports_every_declared_symbol():
 
 def test_strerror_names_every_code():
     lib = ewald.load()
-    for code in range(9):
+    for code in range(10):
         assert lib.ewald_strerror(code) not in (None, b"unknown error")
+
+
+def test_build_flags_tell_the_debug_library_apart():
+    """The release library reports no debug checks; the debug library
+    (-DEWALD_DEBUG, index checks in every kernel) reports them and exports
+    the same entry points."""
+    from paper_2507_02888_gb300 import build
+    assert ewald.load().ewald_build_flags() & 1 == 0
+    if not os.path.exists(build.LIB_DEBUG):
+        pytest.skip("debug library not built (python -m paper_2507_02888_gb300.build --all)")
+    dbg = ctypes.CDLL(build.LIB_DEBUG)
+    dbg.ewald_build_flags.restype = ctypes.c_int
+    assert dbg.ewald_build_flags() & 1 == 1
+    missing = [n for n in declared_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
 
 
 def _create(dim=3, lattice=None, q=(-1.0,), **kw):
