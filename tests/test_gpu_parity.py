@@ -278,9 +278,13 @@ def test_device_pointers_match_host_path(ew):
     assert np.array_equal(de_d.cpu().numpy(), de_h)
 
 
-def test_error_codes(ew):
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
+def test_error_codes(ew, prec):
     w = small_case("sc54", 2)
-    ctx, b = make(ew, w, "fp64")
+    ctx, b = make(ew, w, prec)
+    with pytest.raises(ew.EwaldError) as ei:
+        ew.Batch(ctx, 0)
+    assert ei.value.code == 1                          # an empty batch is refused
     with pytest.raises(ew.EwaldError) as ei:
         b.accept([1, 1])
     assert ei.value.code == 4                          # no pending proposal
