@@ -63,46 +63,78 @@ int apply_tiling(ewald_ctx *c, int S, int bits) {
     free_one(c->dev, s.cxy);
     free_one(c->dev, s.cz);
     free_one(c->dev, s.clist);
+    free_one(c->dev, s.cxy_mv);  // no-ops where they alias the energy kernels' tables
+    free_one(c->dev, s.cz_mv);
+    free_one(c->dev, s.clist_mv);
     free_one(c->dev, s.items);
     s.cand = nullptr;
     s.cxy = nullptr;
     s.cz = nullptr;
     s.clist = nullptr;
+    s.cxy_mv = nullptr;
+    s.cz_mv = nullptr;
+    s.clist_mv = nullptr;
     s.items = nullptr;
     s.sub_bits = t.sub_bits;
     s.cand_max = t.cand_max;
     if ((e = upload(c->dev, (unsigned short **)&s.cand, t.cand.data(), t.cand.size()))) return cuda_fail(c, e);
-    {   // the mixed loop's tables: distinct lists as pairs of FP32 images
+    {   // the mixed loop's tables: distinct lists as pairs of FP32 images;
+        // the move kernel's copy keeps the lists of cand where the energy
+        // kernels' differ (mixed_direct)
         const int np = mixed_pairs(t.cand_max), n_sub = (int)(t.cand.size() / std::max(t.cand_max, 1));
         const int pstride = np | 1;  // odd: consecutive lists start in different banks
-        std::map<std::vector<unsigned short>, int> ids;
-        std::vector<unsigned short> clist(n_sub);
-        std::vector<float4> cxy;
-        std::vector<float2> cz;
         auto imf = [&](int i, int y) {  // FP32 image component, as in the FP32 image table
             return i < s.n_img ? (float)t.img[3 * i + y] : 1e18f;
         };
-        for (int r = 0; r < n_sub; ++r) {
-            std::vector<unsigned short> l(2 * np, (unsigned short)s.n_img);
-            std::copy(t.cand.begin() + (size_t)r * t.cand_max, t.cand.begin() + (size_t)(r + 1) * t.cand_max, l.begin());
-            auto it = ids.find(l);
-            if (it == ids.end()) {
-                it = ids.emplace(l, (int)ids.size()).first;
-                for (int p = 0; p < pstride; ++p) {  // pairs past np: padding between lists
-                    const int a = p < np ? l[2 * p] : s.n_img, b = p < np ? l[2 * p + 1] : s.n_img;
-                    cxy.push_back(make_float4(imf(a, 0), imf(b, 0), imf(a, 1), imf(b, 1)));
-                    cz.push_back(make_float2(t.dim == 3 ? imf(a, 2) : 0.0f, t.dim == 3 ? imf(b, 2) : 0.0f));
+        struct Tables {
+            std::vector<unsigned short> clist;
+            std::vector<float4> cxy;
+            std::vector<float2> cz;
+            int n_lists = 0;
+        };
+        auto tables = [&](const std::vector<unsigned short> &order, Tables &o) {
+            std::map<std::vector<unsigned short>, int> ids;
+            o.clist.assign(n_sub, 0);
+            for (int r = 0; r < n_sub; ++r) {
+                std::vector<unsigned short> l(2 * np, (unsigned short)s.n_img);
+                std::copy(order.begin() + (size_t)r * t.cand_max, order.begin() + (size_t)(r + 1) * t.cand_max,
+                          l.begin());
+                auto it = ids.find(l);
+                if (it == ids.end()) {
+                    it = ids.emplace(l, (int)ids.size()).first;
+                    for (int p = 0; p < pstride; ++p) {  // pairs past np: padding between lists
+                        const int a = p < np ? l[2 * p] : s.n_img, b = p < np ? l[2 * p + 1] : s.n_img;
+                        o.cxy.push_back(make_float4(imf(a, 0), imf(b, 0), imf(a, 1), imf(b, 1)));
+                        o.cz.push_back(make_float2(t.dim == 3 ? imf(a, 2) : 0.0f, t.dim == 3 ? imf(b, 2) : 0.0f));
+                    }
                 }
+                o.clist[r] = (unsigned short)it->second;
             }
-            clist[r] = (unsigned short)it->second;
-        }
-        if (ids.size() > 65535) return fail(c, EWALD_ERR_ARG, "too many distinct candidate lists");
-        s.n_lists = (int)ids.size();
+            o.n_lists = (int)ids.size();
+            return ids.size() <= 65535;
+        };
+        s.mixed_direct = mixed_direct_pays(t) ? 1 : 0;
+        Tables te, tm;
+        if (!tables(mixed_cand_order(t, s.mixed_direct), te) || (s.mixed_direct && !tables(t.cand, tm)))
+            return fail(c, EWALD_ERR_ARG, "too many distinct candidate lists");
+        s.n_lists = te.n_lists;
         s.cand_pairs = np;
         s.cand_pstride = pstride;
-        if ((e = upload(c->dev, (float4 **)&s.cxy, cxy.data(), cxy.size()))) return cuda_fail(c, e);
-        if ((e = upload(c->dev, (float2 **)&s.cz, cz.data(), cz.size()))) return cuda_fail(c, e);
-        if ((e = upload(c->dev, (unsigned short **)&s.clist, clist.data(), clist.size()))) return cuda_fail(c, e);
+        if ((e = upload(c->dev, (float4 **)&s.cxy, te.cxy.data(), te.cxy.size()))) return cuda_fail(c, e);
+        if ((e = upload(c->dev, (float2 **)&s.cz, te.cz.data(), te.cz.size()))) return cuda_fail(c, e);
+        if ((e = upload(c->dev, (unsigned short **)&s.clist, te.clist.data(), te.clist.size()))) return cuda_fail(c, e);
+        if (s.mixed_direct) {
+            s.n_lists_mv = tm.n_lists;
+            if ((e = upload(c->dev, (float4 **)&s.cxy_mv, tm.cxy.data(), tm.cxy.size()))) return cuda_fail(c, e);
+            if ((e = upload(c->dev, (float2 **)&s.cz_mv, tm.cz.data(), tm.cz.size()))) return cuda_fail(c, e);
+            if ((e = upload(c->dev, (unsigned short **)&s.clist_mv, tm.clist.data(), tm.clist.size())))
+                return cuda_fail(c, e);
+        } else {
+            s.n_lists_mv = s.n_lists;
+            s.cxy_mv = s.cxy;
+            s.cz_mv = s.cz;
+            s.clist_mv = s.clist;
+        }
     }
     s.tile = 32 * S;
     s.n_mob_tiles = (t.n_mob + s.tile - 1) / s.tile;
@@ -507,9 +539,10 @@ size_t mixed_table_bytes(const HostTables &t0, int bits) {
     if (bits != t.sub_bits || t.cand.empty()) set_subcells(&t, bits);
     const int np = mixed_pairs(t.cand_max), n_sub = (int)(t.cand.size() / std::max(t.cand_max, 1));
     std::set<std::vector<unsigned short>> lists;
+    const std::vector<unsigned short> mc = mixed_cand_order(t, mixed_direct_pays(t));
     for (int r = 0; r < n_sub; ++r)
-        lists.insert(std::vector<unsigned short>(t.cand.begin() + (size_t)r * t.cand_max,
-                                                 t.cand.begin() + (size_t)(r + 1) * t.cand_max));
+        lists.insert(std::vector<unsigned short>(mc.begin() + (size_t)r * t.cand_max,
+                                                 mc.begin() + (size_t)(r + 1) * t.cand_max));
     return lists.size() * (np | 1) * (t.dim == 3 ? sizeof(float4) + sizeof(float2) : sizeof(float4));
 }
 

@@ -102,13 +102,22 @@ struct SysDev {
     const unsigned short *cand;
     // the same lists for the mixed path's pair loop: each distinct list once,
     // as cand_pairs pairs of FP32 images (X_a, X_b, Y_a, Y_b) and (Z_a, Z_b),
-    // padded with the sentinel; clist[cell] = the cell's list
+    // padded with the sentinel; clist[cell] = the cell's list.  With
+    // mixed_direct the second nearest image to the cell's centre comes second.
     const float4 *cxy;
     const float2 *cz;
     const unsigned short *clist;
     int n_lists, cand_pairs;
     int cand_pstride;  // pairs from one list to the next: odd, so that lanes reading pair p of
                        // different lists fall in different banks of shared memory
+    int mixed_direct;  // the energy kernels' pair loop evaluates each pair's first two images
+                       // (the two nearest to the cell's centre) without the lane rings
+    // the move kernel's copy of these tables, lists in the order of cand (the
+    // same arrays unless mixed_direct reorders the energy kernels' lists)
+    const float4 *cxy_mv;
+    const float2 *cz_mv;
+    const unsigned short *clist_mv;
+    int n_lists_mv;
     int q_uniform;  // every mobile charge equal and every fixed charge equal
     int tile, n_mob_tiles, n_items;  // pair tiles (T = tile) and items per walker
     int real_warps;                  // mixed form: warps per real-space CTA (8 or 16)
@@ -195,6 +204,10 @@ double shortest_lattice_vector(const HostTables &t);
 int short_range_lists(const HostTables &t, double cutoff, int max_bits, std::vector<double> *img,
                       std::vector<unsigned short> *cand, int *bits_out);
 size_t subcell_bytes(const HostTables &t, int bits);
+// The mixed form's candidate lists (mixed_cand_order) and whether its energy
+// loop evaluates their first two images directly (mixed_direct_pays).
+bool mixed_direct_pays(const HostTables &t);
+std::vector<unsigned short> mixed_cand_order(const HostTables &t, bool direct);
 
 // kernels.cu launchers (return cudaError_t as int)
 struct LaunchCfg {

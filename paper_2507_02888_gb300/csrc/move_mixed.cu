@@ -37,12 +37,12 @@ struct ProposeMixedSmem {
         return align16((size_t)(kProposeMixedThreads / 32) * kMoveRing * 32 * sizeof(float) * 2);
     }
     __host__ __device__ static size_t bytes(const SysDev &s) {
-        return MixedImageSmem::bytes(s, s.dim) + ring_bytes() + MoveSmem<float>::table_bytes(s) +
+        return MixedImageSmem::bytes(s, s.dim, true) + ring_bytes() + MoveSmem<float>::table_bytes(s) +
                align16((kProposeMixedThreads / 32) * sizeof(double));
     }
     __device__ void carve(unsigned char *base, const SysDev &s, int dim) {
-        ims.carve(base, s, dim);
-        size_t off = MixedImageSmem::bytes(s, dim);
+        ims.carve(base, s, dim, true);
+        size_t off = MixedImageSmem::bytes(s, dim, true);
         rings = (float *)(base + off);
         off += ring_bytes();
         Cx<float> *p = (Cx<float> *)(base + off);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kProposeMixedThreads)
     __shared__ unsigned long long su[2][3];  // old, new: exact fixed-point coordinates
     ProposeMixedSmem m;
     m.carve(smem, s, DIM);
-    m.ims.stage(s, DIM);
+    m.ims.stage(s, DIM, true);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const TermK32 tk = FP<float>::term_consts(s);
     const int n_other = s.n_mob - 1 + s.n_fix;

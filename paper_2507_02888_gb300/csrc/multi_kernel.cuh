@@ -47,6 +47,21 @@ __device__ inline int count_done(int *p) {
     return old;
 }
 
+// A specialized kernel's FP32 pair item: the system's mixed_direct as a
+// compile-time choice per item (uniform over the CTA), as in the
+// single-system kernel's instantiations
+template <int DIM, int CM>
+__device__ __forceinline__ void multi_real_cm(const SysDev &ss, const BatchDev &sb, int w, int p,
+                                              const MixedImageSmem &ims, unsigned char *work, int js) {
+    if constexpr (CM >= 4) {
+        if (ss.mixed_direct) {
+            real_item_mixed_cm<DIM, CM, false, kDirectAlways>(ss, sb, w, p, ims, work, js);
+            return;
+        }
+    }
+    real_item_mixed_cm<DIM, CM, false, kDirectNever>(ss, sb, w, p, ims, work, js);
+}
+
 template <typename R, int DIMX, int CMA, int CMB, bool QWX>
 __device__ __forceinline__ void multi_real(const SysDev &ss, const BatchDev &sb, int w, int p,
                                            const typename std::conditional<sizeof(R) == 4, MixedImageSmem,
@@ -59,8 +74,8 @@ __device__ __forceinline__ void multi_real(const SysDev &ss, const BatchDev &sb,
         if (ss.dim == 3) real_item_mixed<3>(ss, sb, w, p, ims, work, js);
         else real_item_mixed<2>(ss, sb, w, p, ims, work, js);
     } else {
-        if (mixed_cm(ss.cand_max) == CMA) real_item_mixed_cm<DIMX, CMA, false>(ss, sb, w, p, ims, work, js);
-        else real_item_mixed_cm<DIMX, (CMB < 0 ? CMA : CMB), false>(ss, sb, w, p, ims, work, js);
+        if (mixed_cm(ss.cand_max) == CMA) multi_real_cm<DIMX, CMA>(ss, sb, w, p, ims, work, js);
+        else multi_real_cm<DIMX, (CMB < 0 ? CMA : CMB)>(ss, sb, w, p, ims, work, js);
     }
 }
 

@@ -6,7 +6,9 @@
 
 namespace ewald {
 
-template <int DIM, int CM, bool QW>
+// DIRECT: the system's mixed_direct, as a compile-time choice (the first
+// two images of each pair evaluated without the lane rings, CM = 4 ... 8)
+template <int DIM, int CM, bool QW, bool DIRECT = false>
 __global__ void __launch_bounds__(kRealMixedThreads, kRealMinBlocksMixed) k_real_mixed(SysDev s, BatchDev b) {
     extern __shared__ __align__(32) unsigned char smem[];
     MixedImageSmem ims;
@@ -18,27 +20,29 @@ __global__ void __launch_bounds__(kRealMixedThreads, kRealMinBlocksMixed) k_real
         const int w = (int)(item / s.n_items), p = (int)(item - (long long)w * s.n_items);
         // units of 32 x 8 pairs (16 warps) or 32 x 16 (8 warps): a 256 x 256
         // item splits evenly over the CTA's warps
-        real_item_mixed_cm<DIM, CM, QW>(s, b, w, p, ims, work, s.real_warps / 4);
+        real_item_mixed_cm<DIM, CM, QW, DIRECT ? kDirectAlways : kDirectNever>(s, b, w, p, ims, work,
+                                                                             s.real_warps / 4);
     }
 }
 
 using RealFn = void (*)(SysDev, BatchDev);
 
 template <int DIM, bool QW>
-static RealFn pick_cm(int cm) {
+static RealFn pick_cm(int cm, bool direct) {
     switch (cm) {
         case 2: return k_real_mixed<DIM, 2, QW>;
-        case 4: return k_real_mixed<DIM, 4, QW>;
-        case 6: return k_real_mixed<DIM, 6, QW>;
-        case 8: return k_real_mixed<DIM, 8, QW>;
+        case 4: return direct ? k_real_mixed<DIM, 4, QW, true> : k_real_mixed<DIM, 4, QW>;
+        case 6: return direct ? k_real_mixed<DIM, 6, QW, true> : k_real_mixed<DIM, 6, QW>;
+        case 8: return direct ? k_real_mixed<DIM, 8, QW, true> : k_real_mixed<DIM, 8, QW>;
         default: return k_real_mixed<DIM, 0, QW>;
     }
 }
 
 static RealFn real_mixed_fn(const SysDev &s) {
     const int cm = mixed_cm(s.cand_max);
-    if (s.dim == 3) return s.q_uniform ? pick_cm<3, false>(cm) : pick_cm<3, true>(cm);
-    return s.q_uniform ? pick_cm<2, false>(cm) : pick_cm<2, true>(cm);
+    const bool d = s.mixed_direct != 0;
+    if (s.dim == 3) return s.q_uniform ? pick_cm<3, false>(cm, d) : pick_cm<3, true>(cm, d);
+    return s.q_uniform ? pick_cm<2, false>(cm, d) : pick_cm<2, true>(cm, d);
 }
 
 int configure_real_mixed(const SysDev &s, size_t smem, int *blocks_per_sm) {

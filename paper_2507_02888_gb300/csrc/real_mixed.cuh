@@ -20,6 +20,11 @@
 // are drained at the end of the item.  Compared with a warp-wide queue this
 // removes the per-candidate ballot, population counts and ring addressing,
 // which were a third of the loop's instructions.
+// Where a system's lists hold 3 to 8 images and their second image (the
+// second nearest to the cell's centre) is inside r_c for most displacements
+// (SysDev::mixed_direct, decided at set-up), the first two images of every
+// pair skip the ring: one paired evaluation with the images outside r_c
+// masked to zero.
 //
 // Charges: when every mobile charge is equal and every fixed charge is
 // equal (the electron gases and the ionic solids), an item's pairs share
@@ -32,6 +37,8 @@
 namespace ewald {
 
 constexpr int kLaneRing = 32;  // pending terms per lane (a power of two)
+// how the pair loop takes the first two images of a list (see pair_ring)
+constexpr int kDirectNever = 0, kDirectFlag = 1, kDirectAlways = 2;
 
 // A particle of the FP32 pair loop in shared memory: the top 32 bits of the
 // fixed-point coordinates and the charge; in a 2D cell the third word holds
@@ -47,28 +54,37 @@ struct __align__(16) Tile16 {
 // paired FP32 instructions: for pair p of list L, xy[L][p] = (X_a, X_b,
 // Y_a, Y_b) and, in 3D, z[L][p] = (Z_a, Z_b) (lists padded with the far
 // sentinel to cand_pairs pairs, stored cand_pstride pairs apart); clist[cell]
-// is the cell's list.
+// is the cell's list.  moves: the move kernel's copy of the tables (lists in
+// the order of the FP64 tables; the energy kernels' copy differs where the
+// system takes the first two images directly, SysDev::mixed_direct).
 struct MixedImageSmem {
     float4 *xy;
     float2 *z;
     unsigned short *clist;
-    __host__ __device__ static size_t bytes(const SysDev &s, int dim) {
-        const size_t n_sub = (size_t)1 << (s.sub_bits * dim), np = (size_t)s.n_lists * s.cand_pstride;
+    int n_lists;  // distinct lists staged
+    __host__ __device__ static int lists(const SysDev &s, bool moves) { return moves ? s.n_lists_mv : s.n_lists; }
+    __host__ __device__ static size_t bytes(const SysDev &s, int dim, bool moves = false) {
+        const size_t n_sub = (size_t)1 << (s.sub_bits * dim), np = (size_t)lists(s, moves) * s.cand_pstride;
         return align16(np * sizeof(float4)) + (dim == 3 ? align16(np * sizeof(float2)) : 0) +
                align16(n_sub * sizeof(unsigned short));
     }
-    __device__ void carve(unsigned char *base, const SysDev &s, int dim) {
-        const size_t np = (size_t)s.n_lists * s.cand_pstride;
+    __device__ void carve(unsigned char *base, const SysDev &s, int dim, bool moves = false) {
+        n_lists = lists(s, moves);
+        const size_t np = (size_t)n_lists * s.cand_pstride;
         xy = (float4 *)base;
         z = (float2 *)(base + align16(np * sizeof(float4)));
         clist = (unsigned short *)(base + align16(np * sizeof(float4)) + (dim == 3 ? align16(np * sizeof(float2)) : 0));
     }
-    __device__ void stage(const SysDev &s, int dim) {
-        const int n_sub = 1 << (s.sub_bits * dim), np = s.n_lists * s.cand_pstride;
-        for (int i = threadIdx.x; i < np; i += blockDim.x) xy[i] = s.cxy[i];
+    // after carve with the same moves
+    __device__ void stage(const SysDev &s, int dim, bool moves = false) {
+        const int n_sub = 1 << (s.sub_bits * dim), np = n_lists * s.cand_pstride;
+        const float4 *gxy = moves ? s.cxy_mv : s.cxy;
+        const float2 *gz = moves ? s.cz_mv : s.cz;
+        const unsigned short *gl = moves ? s.clist_mv : s.clist;
+        for (int i = threadIdx.x; i < np; i += blockDim.x) xy[i] = gxy[i];
         if (dim == 3)
-            for (int i = threadIdx.x; i < np; i += blockDim.x) z[i] = s.cz[i];
-        for (int i = threadIdx.x; i < n_sub; i += blockDim.x) clist[i] = s.clist[i];
+            for (int i = threadIdx.x; i < np; i += blockDim.x) z[i] = gz[i];
+        for (int i = threadIdx.x; i < n_sub; i += blockDim.x) clist[i] = gl[i];
     }
 };
 
@@ -239,9 +255,20 @@ __device__ __forceinline__ float4 lds128(const float4 *p) {
 // r^2 that pass; FIRST: the pairs start with candidate 0, the only image
 // through which a displacement of the cell can come within the close
 // radius: a close pair is recorded for FP64 instead.
-template <int DIM, int NP, bool FIRST, bool QW, int CAP>
+// DIRECT_OK and direct (the system's mixed_direct): the first pair of
+// images, the two nearest to the cell's centre, is evaluated at once as one
+// paired term (images outside r_c, or close, contribute exactly zero)
+// instead of entering the ring.  Measured on the GB300 (fcc N = 1024, 4096
+// walkers): k_real_mixed 21.98 -> 20.86 ms, diamond +6%.  In the move
+// kernel, which services its rings after every pair, it did not pay
+// (propose 0.173 ms per round against 0.166), and the reordered lists alone
+// slowed it to 0.178 ms: the move kernel keeps every image in the ring and
+// its own copy of the tables in the original order (0.167 ms).
+template <int DIM, int NP, bool FIRST, bool QW, int CAP, bool DIRECT_OK = false>
 __device__ __forceinline__ void test_pairs(const float4 *xy, const float2 *zz, const float *x, float z2, float rc2,
-                                           float close2, float wgt, LaneRing<QW, CAP> &ring, bool &close) {
+                                           float close2, float wgt, LaneRing<QW, CAP> &ring, bool &close,
+                                           bool direct = false, Acc<float> *acc = nullptr,
+                                           const TermK32 *tk = nullptr) {
     const float2 x0 = splat(x[0]), x1 = splat(x[1]), zs = splat(z2);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -258,8 +285,16 @@ __device__ __forceinline__ void test_pairs(const float4 *xy, const float2 *zz, c
             close = pa && r2.x < close2;
             pa = pa && !close;
         }
-        ring.push(pa, r2.x, wgt);
-        ring.push(pb, r2.y, wgt);
+        if (FIRST && DIRECT_OK && p == 0 && direct) {  // uniform over the warp (one system)
+            // masked entries take r^2 = 1 (a finite term) and then weigh zero
+            float2 t = erfc_over_r_f32x2(make_float2(pa ? r2.x : 1.0f, pb ? r2.y : 1.0f), *tk);
+            t = make_float2(pa ? t.x : 0.0f, pb ? t.y : 0.0f);
+            if (QW) t = mul2(t, splat(wgt));
+            acc->add2(t);
+        } else {
+            ring.push(pa, r2.x, wgt);
+            ring.push(pb, r2.y, wgt);
+        }
     }
 }
 
@@ -291,8 +326,12 @@ constexpr int kPairsPerService = CM == 0 ? 1 : CM == 2 ? 8 : 2;
 // The images of one pair of particles: CM candidate slots (CM = 2 ... 8
 // compile-time; the caller services the rings every kPairsPerService<CM>
 // pairs) or, CM = 0, the list in chunks of 8 pairs (serviced here after
-// every chunk but the last, which the caller's service follows)
-template <int DIM, int CM, bool QW, int CAP>
+// every chunk but the last, which the caller's service follows).
+// DIRECT: how the first two images of a list are taken (CM = 4 ... 8):
+// kDirectNever (through the ring: the move kernel), kDirectFlag (without the
+// ring where the system's mixed_direct is set: the multi-system kernels) or
+// kDirectAlways (the single-system kernel's instantiation for such systems).
+template <int DIM, int CM, bool QW, int CAP, int DIRECT = kDirectNever>
 __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem &ims, const Tile16 &a,
                                           const Tile16 &b, bool valid, float wgt, LaneRing<QW, CAP> &ring,
                                           bool &close, Acc<float> &acc, const TermK32 &tk) {
@@ -301,11 +340,14 @@ __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem 
     const float rc2 = valid ? s.rc2_f : 0.0f;  // invalid lanes never pass
     const int sub = EWALD_IN_RANGE(sc < (1 << (s.sub_bits * DIM)), ring.status) ? sc : 0;
     const int lid = ims.clist[sub];
-    const int base = (EWALD_IN_RANGE(lid < s.n_lists, ring.status) ? lid : 0) * s.cand_pstride;
+    const int base = (EWALD_IN_RANGE(lid < ims.n_lists, ring.status) ? lid : 0) * s.cand_pstride;
     const float4 *xy = ims.xy + base;
     const float2 *zz = ims.z + base;
     if (CM > 0) {
-        test_pairs<DIM, CM / 2, true, QW, CAP>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
+        constexpr bool ok = DIRECT != kDirectNever && CM >= 4;
+        const bool direct = DIRECT == kDirectAlways || (DIRECT == kDirectFlag && s.mixed_direct != 0);
+        test_pairs<DIM, CM / 2, true, QW, CAP, ok>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close, direct, &acc,
+                                                   &tk);
     } else {
         constexpr int CP = kChunkPairs<CAP>;
         test_pairs<DIM, CP, true, QW, CAP>(xy, zz, x, z2, rc2, s.close2_f, wgt, ring, close);
@@ -318,10 +360,12 @@ __device__ __forceinline__ void pair_ring(const SysDev &s, const MixedImageSmem 
 }
 
 // The rings' service after the PAIRS pairs of a step (the energy kernels:
-// kPairsPerService; the move kernel services after every pair)
-template <int CM, int PAIRS = kPairsPerService<CM>, bool QW, int CAP>
+// kPairsPerService; the move kernel services after every pair).  PUSHED:
+// the images of a pair that may enter the ring (CM, or CM - 2 when the
+// first two are always evaluated directly).
+template <int CM, int PAIRS = kPairsPerService<CM>, int PUSHED = CM, bool QW, int CAP>
 __device__ __forceinline__ void ring_service(LaneRing<QW, CAP> &ring, Acc<float> &acc, const TermK32 &tk) {
-    constexpr int room = CM > 0 ? CM * PAIRS : 2 * kChunkPairs<CAP>;
+    constexpr int room = CM > 0 ? PUSHED * PAIRS : 2 * kChunkPairs<CAP>;
     ring.template service<room>(acc, tk);
 }
 
@@ -331,7 +375,7 @@ __device__ __forceinline__ void ring_service(LaneRing<QW, CAP> &ring, Acc<float>
 // Units are 32 x 32 sub-tiles (diagonal tiles: the upper triangle), or
 // jsplit slices of one, taken by the warps in turn; each warp sums its
 // units, and the item's sum adds the warps' sums in warp order.
-template <int DIM, int CM, bool QW>
+template <int DIM, int CM, bool QW, int DIRECT = kDirectFlag>
 __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, int p, const MixedImageSmem &ims,
                                    unsigned char *work, int jsplit) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -395,9 +439,10 @@ __device__ void real_item_mixed_cm(const SysDev &s, const BatchDev &b, int w, in
             const bool valid = vi && (!self || lane < jj);
             const float wgt = QW ? pi.q * pj.q : 1.0f;
             bool close = false;
-            pair_ring<DIM, CM, QW, kLaneRing>(s, ims, pi, pj, valid, wgt, ring, close, acc, tk);
+            pair_ring<DIM, CM, QW, kLaneRing, DIRECT>(s, ims, pi, pj, valid, wgt, ring, close, acc, tk);
             if ((jj - j_lo) % kPairsPerService<CM> == kPairsPerService<CM> - 1 || jj + 1 == j_end)
-                ring_service<CM>(ring, acc, tk);
+                ring_service<CM, kPairsPerService<CM>, (DIRECT == kDirectAlways && CM >= 4) ? CM - 2 : CM>(ring, acc,
+                                                                                                         tk);
             const unsigned cb = __ballot_sync(0xffffffffu, close);
             if (cb) {  // uniform over the warp, rare
                 const int at = cl.n + __popc(cb & ((1u << lane) - 1u));

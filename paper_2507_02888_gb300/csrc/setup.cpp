@@ -225,6 +225,83 @@ static int cand_lists(const HostTables &t, const std::vector<double> &imgs, doub
     return longest;
 }
 
+// Position in list l (of length len) of the image second nearest to the
+// point c, after the nearest, which t.cand already puts first.
+static int second_nearest(const HostTables &t, const unsigned short *l, int len, const double *c) {
+    const int n_img = (int)t.img.size() / 3;
+    int best = 1;
+    double db = 1e300;
+    for (int p = 1; p < len; ++p) {
+        if (l[p] >= n_img) continue;
+        double x[3];
+        for (int y = 0; y < 3; ++y) x[y] = c[y] + t.img[3 * l[p] + y];
+        const double r = norm_n(x, t.dim);
+        if (r < db) db = r, best = p;
+    }
+    return best;
+}
+
+static void cell_centre(const HostTables &t, int s, double *c) {
+    const int M = 1 << t.sub_bits;
+    double f[3] = {0, 0, 0};
+    for (int k = 0; k < t.dim; ++k) f[k] = -0.5 + (((s >> (k * t.sub_bits)) & (M - 1)) + 0.5) / M;
+    lat_to_cart(t, f, c);
+}
+
+// Whether the mixed form's energy loop should take the first two images of
+// every list as one unconditional paired evaluation (terms outside r_c
+// masked): where lists hold 3 to 8 images and the second nearest image to a
+// cell's centre lies inside r_c for at least 3/4 of the displacements, the
+// masked evaluation costs less than testing and queueing the two images.
+// Estimated on 4^dim stratified points of every displacement cell.
+bool mixed_direct_pays(const HostTables &t) {
+    if (t.cand_max < 3 || t.cand_max > 8) return false;
+    const int dim = t.dim, M = 1 << t.sub_bits, L = t.cand_max, n_sub = (int)(t.cand.size() / L);
+    const int per = 1 << (2 * dim);
+    long inside = 0, total = 0;
+    for (int s = 0; s < n_sub; ++s) {
+        const int len = t.cand_len.empty() ? L : t.cand_len[s];
+        double c[3];
+        cell_centre(t, s, c);
+        const unsigned short *l = t.cand.data() + (size_t)s * L;
+        const int p2 = len >= 2 ? second_nearest(t, l, len, c) : -1;
+        for (int q = 0; q < per; ++q) {
+            total++;
+            if (p2 < 0 || l[p2] >= (int)t.img.size() / 3) continue;
+            double f[3] = {0, 0, 0}, x[3];
+            for (int k = 0; k < dim; ++k) {
+                const int cell_k = (s >> (k * t.sub_bits)) & (M - 1), sub_k = (q >> (2 * k)) & 3;
+                f[k] = -0.5 + (cell_k + (sub_k + 0.5) / 4) / M;
+            }
+            lat_to_cart(t, f, x);
+            for (int y = 0; y < 3; ++y) x[y] += t.img[3 * l[p2] + y];
+            if (norm_n(x, dim) < t.r_c) inside++;
+        }
+    }
+    return total > 0 && inside * 4 >= total * 3;
+}
+
+// The candidate lists in the order of the mixed form's pair loop: as in
+// t.cand (the image nearest to the cell's centre first, the rest in
+// image-table order), and with direct evaluation the second nearest image
+// moved to the second place, so that the unconditional pair holds the two
+// images most often inside r_c.
+std::vector<unsigned short> mixed_cand_order(const HostTables &t, bool direct) {
+    std::vector<unsigned short> out = t.cand;
+    if (!direct) return out;
+    const int L = std::max(t.cand_max, 1), n_sub = (int)(t.cand.size() / L);
+    for (int s = 0; s < n_sub; ++s) {
+        const int len = t.cand_len.empty() ? L : t.cand_len[s];
+        if (len < 3) continue;
+        double c[3];
+        cell_centre(t, s, c);
+        unsigned short *l = out.data() + (size_t)s * L;
+        const int p2 = second_nearest(t, l, len, c);
+        std::rotate(l + 1, l + p2, l + p2 + 1);
+    }
+    return out;
+}
+
 static int build_cand(const HostTables &t, int bits, std::vector<unsigned short> *cand, std::vector<int> *len) {
     return cand_lists(t, t.img, t.r_c, bits, cand, len);
 }
