@@ -191,11 +191,12 @@ REAL_SOURCES = ["paper_2507_02888_gb300/csrc/real_mixed.cu", "paper_2507_02888_g
 def real_kernel_name(info, w):
     """The k_real_mixed instantiation the library launches for this system:
     candidate slots rounded up to 2, 4, 6 or 8 (0: longer lists, walked in
-    chunks), and whether the pair weights vary (the mobile or the fixed
-    charges not all equal in FP32)."""
+    chunks), whether the pair weights vary (the mobile or the fixed charges
+    not all equal in FP32) and whether the first two images of a pair are
+    evaluated without the lane rings (mixed_direct)."""
     cm = next((c for c in (2, 4, 6, 8) if info["max_candidates"] <= c), 0)
     qw = int(any(len(q) and np.ptp(np.asarray(q, dtype=np.float32)) != 0 for q in (w["q"], w["fixed_q"])))
-    return "k_real_mixed<%d,%d,%d>" % (info["dim"], cm, qw)
+    return "k_real_mixed<%d,%d,%d,%d>" % (info["dim"], cm, qw, int(info.get("mixed_direct", 0)))
 
 
 def profiled_traffic(workload, precision):

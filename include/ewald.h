@@ -113,6 +113,10 @@ typedef struct {
                              g(z) = z erf(alpha z) + exp(-alpha^2 z^2)/(alpha sqrt(pi)) */
     double e_fixed_real;  /* real-space pair sum among fixed particles */
     int n_layers;         /* distinct particle heights (1 unless the desc gave heights) */
+    int mixed_direct;     /* mixed form: 1 if the energy kernels' pair loop evaluates the two
+                             images nearest to each displacement cell's centre as one masked
+                             term without testing them first (chosen at set-up where those two
+                             lie inside r_cutoff for at least 3/4 of the displacements), else 0 */
 } ewald_info;
 
 /* Create a context: validates the description, builds the G list, the image

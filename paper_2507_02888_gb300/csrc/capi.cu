@@ -677,6 +677,7 @@ int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
     i->e_background = t.e_bg;
     i->e_fixed_real = t.e_II;
     i->n_layers = t.n_layers;
+    i->mixed_direct = c->s.mixed_direct;
     return EWALD_OK;
 }
 

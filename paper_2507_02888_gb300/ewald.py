@@ -48,7 +48,8 @@ class Info(ctypes.Structure):
                 ("volume", _c_double), ("n_g_half", _c_int), ("n_images", _c_int),
                 ("subcell_bits", _c_int), ("pair_tile", _c_int), ("max_candidates", _c_int), ("n_runs", _c_int),
                 ("run_len", _c_int), ("e_madelung", _c_double), ("e_self", _c_double),
-                ("e_background", _c_double), ("e_fixed_real", _c_double), ("n_layers", _c_int)]
+                ("e_background", _c_double), ("e_fixed_real", _c_double), ("n_layers", _c_int),
+                ("mixed_direct", _c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
