@@ -152,18 +152,21 @@ def test_mixed_direct_choice(ew):
     loops: on where lists hold 3 to 8 images and the second nearest image
     to a displacement cell's centre is inside r_c for >= 3/4 of the
     displacements (sc40 with mixed charges and the clustered sc80: ~0.99,
-    with weighted terms and close pairs; the 1024-electron fcc gas: 0.91),
-    off where it is not (fcc100: ~0.65, diamond1: ~0.7), where lists are
-    short (2D hexagonal) or long (sc54: chunked lists)."""
-    want = {"mixed_q": 1, "clustered": 1, "fcc100": 0, "diamond1": 0, "hex70": 0, "sc54": 0}
+    with weighted terms and close pairs; hex70 in 2D: ~0.9; the
+    1024-electron fcc gas: 0.91), off where it is not (fcc100: ~0.65,
+    diamond1: ~0.7), where lists are short (the 338-electron 2D gas: one
+    or two images) or long (sc54: chunked lists)."""
+    want = {"mixed_q": 1, "clustered": 1, "hex70": 1, "fcc100": 0, "diamond1": 0, "sc54": 0}
     for name, flag in want.items():
         ctx = ew.context_for(small_case(name, 2), precision="mixed")
         assert ctx.info()["mixed_direct"] == flag, name
         ctx.close()
-    ctx = ew.context_for(I.workload("heg3d_fcc_n1024", 2), precision="mixed")
-    info = ctx.info()
-    assert info["mixed_direct"] == 1 and 3 <= info["max_candidates"] <= 8
-    ctx.close()
+    for name, flag in (("heg3d_fcc_n1024", 1), ("heg2d_hex_n338", 0)):
+        ctx = ew.context_for(I.workload(name, 2), precision="mixed")
+        info = ctx.info()
+        assert info["mixed_direct"] == flag, name
+        assert not flag or 3 <= info["max_candidates"] <= 8
+        ctx.close()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
