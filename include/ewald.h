@@ -128,6 +128,17 @@ typedef struct {
 int ewald_create(const ewald_desc *desc, void *cuda_stream, ewald_ctx **out);
 void ewald_destroy(ewald_ctx *ctx);
 int ewald_get_info(const ewald_ctx *ctx, ewald_info *info);
+
+/* Plan a context without creating it: runs the same host set-up as
+ * ewald_create (validation, cutoffs, G list, image and candidate lists,
+ * constants, all in FP64; paper Sec. 6.1) and its default real-space tiling,
+ * and fills *info as ewald_get_info would for the new context.  Touches no
+ * GPU and allocates no device memory, so it also works on a machine without
+ * one (sizing, manifests, tests of the set-up).  A tiling cached through
+ * EWALD_TUNE_CACHE is not applied.  Errors: those of ewald_create's
+ * validation (EWALD_ERR_ARG, EWALD_ERR_OOM); EWALD_ERR_ARG for a NULL
+ * argument.  info is caller-owned host memory. */
+int ewald_plan(const ewald_desc *desc, ewald_info *info);
 /* The half-space G list in the library's storage order: nvec[n_g_half][dim]
  * integer coordinates on the reciprocal basis (host memory). */
 int ewald_get_gvectors(const ewald_ctx *ctx, int *nvec);

@@ -160,6 +160,31 @@ int apply_config(ewald_ctx *c, int S, int bits, int warps, int chunks) {
     return apply_tiling(c, S, bits);
 }
 
+// The real-space tiling a context starts with (the autotuner or its cache
+// may change it): pair tiles of 32 x S particles per side, 2^bits
+// displacement cells per axis and, for the mixed form, warps per real-space
+// CTA (0: not the mixed form).  The largest item count (S = 1) sizes the
+// batches' partial-sum buffers, so any tiling fits later.
+static void default_tiling(const HostTables &t, int *S_out, int *bits_out, int *warps_out) {
+    int S = t.n_mob >= 128 ? 4 : (t.n_mob >= 64 ? 2 : 1);
+    int bits = t.sub_bits, warps = 0;
+    if (t.precision == EWALD_MIXED) {
+        // the mixed form's pair loop takes 256-particle tiles (no limit on
+        // the units of an item: a quarter of the item boundaries) where they
+        // pad the pairs no more than 128-particle tiles do
+        auto padded = [&](int T) { return std::ceil(t.n_mob / (double)T) * T; };
+        if (t.n_mob >= 256 && padded(256) <= padded(128)) S = 8;
+        // and candidate tables that leave room for its CTAs
+        while (bits > t.min_bits && mixed_table_bytes(t, bits) > kMixedTableBytes) --bits;
+        // CTAs of 16 warps for 256-particle tiles, 8 for smaller ones (an item
+        // then still gives every warp several units)
+        warps = S == 8 ? 16 : 8;
+    }
+    *S_out = S;
+    *bits_out = bits;
+    *warps_out = warps;
+}
+
 int build_device(ewald_ctx *c) {
     HostTables &t = c->t;
     SysDev &s = c->s;
@@ -301,22 +326,9 @@ int build_device(ewald_ctx *c) {
         if ((e = upload(o, (double **)&s.gwl_d, t.gwl.data(), t.gwl.size()))) return cuda_fail(c, e);
         if ((e = upload(o, (float **)&s.gwl_f, gwlf.data(), gwlf.size()))) return cuda_fail(c, e);
     }
-    // pair tiles of 32 x S particles per side; the largest item count (S = 1)
-    // sizes the batches' partial-sum buffers, so any tiling fits later
-    int S = t.n_mob >= 128 ? 4 : (t.n_mob >= 64 ? 2 : 1);
-    int bits = t.sub_bits;
-    if (t.precision == EWALD_MIXED) {
-        // the mixed form's pair loop takes 256-particle tiles (no limit on
-        // the units of an item: a quarter of the item boundaries) where they
-        // pad the pairs no more than 128-particle tiles do
-        auto padded = [&](int T) { return std::ceil(t.n_mob / (double)T) * T; };
-        if (t.n_mob >= 256 && padded(256) <= padded(128)) S = 8;
-        // and candidate tables that leave room for its CTAs
-        while (bits > t.min_bits && mixed_table_bytes(t, bits) > kMixedTableBytes) --bits;
-        // CTAs of 16 warps for 256-particle tiles, 8 for smaller ones (an item
-        // then still gives every warp several units)
-        s.real_warps = S == 8 ? 16 : 8;
-    }
+    int S, bits, warps;
+    default_tiling(t, &S, &bits, &warps);
+    if (warps > 0) s.real_warps = warps;
     {
         int nt1 = (t.n_mob + 31) / 32, nf1 = (t.n_fix + 31) / 32;
         c->max_items = nt1 * (nt1 + 1) / 2 + nt1 * nf1;
@@ -654,9 +666,8 @@ void ewald_destroy(ewald_ctx *c) {
     destroy_now(c);
 }
 
-int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
-    if (!c || !i) return EWALD_ERR_ARG;
-    const HostTables &t = c->t;
+// ewald_info of host tables t with pair tiles of `tile` particles per side
+static void fill_info(const HostTables &t, int tile, int mixed_direct, ewald_info *i) {
     i->dim = t.dim;
     i->n_mobile = t.n_mob;
     i->n_fixed = t.n_fix;
@@ -668,7 +679,7 @@ int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
     i->n_g_half = (int)t.g2slot.size();
     i->n_images = (int)t.img.size() / 3;
     i->subcell_bits = t.sub_bits;
-    i->pair_tile = c->s.tile;
+    i->pair_tile = tile;
     i->max_candidates = t.cand_max;
     i->n_runs = (int)t.runs.size() / 4;
     i->run_len = t.run_len;
@@ -677,7 +688,26 @@ int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
     i->e_background = t.e_bg;
     i->e_fixed_real = t.e_II;
     i->n_layers = t.n_layers;
-    i->mixed_direct = c->s.mixed_direct;
+    i->mixed_direct = mixed_direct;
+}
+
+int ewald_get_info(const ewald_ctx *c, ewald_info *i) {
+    if (!c || !i) return EWALD_ERR_ARG;
+    fill_info(c->t, c->s.tile, c->s.mixed_direct, i);
+    return EWALD_OK;
+}
+
+int ewald_plan(const ewald_desc *desc, ewald_info *i) {
+    EWALD_NVTX("ewald_plan");
+    if (!desc || !i) return EWALD_ERR_ARG;
+    HostTables t;
+    std::string why;
+    const int st = build_tables(desc, &t, &why);
+    if (st) return st;
+    int S, bits, warps;
+    default_tiling(t, &S, &bits, &warps);
+    if (bits != t.sub_bits || t.cand.empty()) set_subcells(&t, bits);
+    fill_info(t, 32 * S, mixed_direct_pays(t) ? 1 : 0, i);
     return EWALD_OK;
 }
 

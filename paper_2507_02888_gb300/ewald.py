@@ -76,6 +76,7 @@ SIGNATURES = [
     ("ewald_create", _c_int, [ctypes.POINTER(Desc), _vp, ctypes.POINTER(_vp)]),
     ("ewald_destroy", None, [_vp]),
     ("ewald_get_info", _c_int, [_vp, ctypes.POINTER(Info)]),
+    ("ewald_plan", _c_int, [ctypes.POINTER(Desc), ctypes.POINTER(Info)]),
     ("ewald_get_gvectors", _c_int, [_vp, _vp]),
     ("ewald_last_error", _c_int, [_vp]),
     ("ewald_strerror", ctypes.c_char_p, [_c_int]),
@@ -172,6 +173,51 @@ def _ptr(x):
     return ctypes.c_void_p(x.ctypes.data), 0
 
 
+def _desc(dim, lattice, mobile_charge, fixed_pos=None, fixed_charge=None, alpha=0.0, g_cutoff=0.0, r_cutoff=0.0,
+          precision="fp64", resum_every=0, mobile_z=None, fixed_z=None):
+    """An ewald_desc and the arrays it points into (keep them alive while it is used)."""
+    dim = int(dim)
+    lat = _f64(lattice, dim * dim)
+    qm = _f64(mobile_charge)
+    nf = 0 if fixed_charge is None else len(fixed_charge)
+    fp = _f64(fixed_pos if nf else np.zeros(1))
+    fq = _f64(fixed_charge if nf else np.zeros(1))
+    prec = PRECISIONS.get(precision, precision)
+    # heights of a layered 2D cell (None: every particle in the plane)
+    zm = None if mobile_z is None else _f64(mobile_z)
+    zf = None if fixed_z is None or nf == 0 else _f64(fixed_z)
+    d = Desc(dim, lat.ctypes.data_as(_dp), len(qm), qm.ctypes.data_as(_dp), nf, fp.ctypes.data_as(_dp),
+             fq.ctypes.data_as(_dp), float(alpha), float(g_cutoff), float(r_cutoff), int(prec), int(resum_every),
+             None if zm is None else zm.ctypes.data_as(_dp), None if zf is None else zf.ctypes.data_as(_dp))
+    return d, (lat, qm, fp, fq, zm, zf)
+
+
+def plan(dim, lattice, mobile_charge, fixed_pos=None, fixed_charge=None, alpha=0.0, g_cutoff=0.0, r_cutoff=0.0,
+         precision="fp64", resum_every=0, mobile_z=None, fixed_z=None):
+    """ewald_plan: the info dict a context of this description would report,
+    from the host set-up alone (no GPU needed)."""
+    lib = load()
+    d, keep = _desc(dim, lattice, mobile_charge, fixed_pos, fixed_charge, alpha, g_cutoff, r_cutoff, precision,
+                    resum_every, mobile_z, fixed_z)
+    i = Info()
+    _check(lib.ewald_plan(ctypes.byref(d), ctypes.byref(i)))
+    del keep
+    return i.as_dict()
+
+
+def plan_for(workload, precision="fp64", **kw):
+    """ewald_plan for a workload dict from paper_2507_02888_gb300.inputs."""
+    w = workload
+    if "z" in w and "mobile_z" not in kw:
+        kw["mobile_z"] = w["z"]
+        if len(w["fixed_q"]) and "fixed_z" in w:
+            kw["fixed_z"] = w["fixed_z"]
+    alpha = kw.pop("alpha", w["alpha"])
+    nf = len(w["fixed_q"])
+    return plan(w["dim"], w["lattice"], w["q"], w["fixed_pos"] if nf else None, w["fixed_q"] if nf else None,
+                alpha=alpha, precision=precision, **kw)
+
+
 class Context:
     """One periodic system: cell, charges, alpha, cutoffs and precision."""
 
@@ -180,20 +226,11 @@ class Context:
                  fixed_z=None):
         lib = load()
         self.dim = int(dim)
-        self._lat = _f64(lattice, self.dim * self.dim)
-        self._qm = _f64(mobile_charge)
+        d, keep = _desc(dim, lattice, mobile_charge, fixed_pos, fixed_charge, alpha, g_cutoff, r_cutoff,
+                        precision, resum_every, mobile_z, fixed_z)
+        self._lat, self._qm, self._fp, self._fq, self._zm, self._zf = keep
         nf = 0 if fixed_charge is None else len(fixed_charge)
-        self._fp = _f64(fixed_pos if nf else np.zeros(1))
-        self._fq = _f64(fixed_charge if nf else np.zeros(1))
         prec = PRECISIONS.get(precision, precision)
-        # heights of a layered 2D cell (None: every particle in the plane)
-        self._zm = None if mobile_z is None else _f64(mobile_z)
-        self._zf = None if fixed_z is None or nf == 0 else _f64(fixed_z)
-        d = Desc(self.dim, self._lat.ctypes.data_as(_dp), len(self._qm), self._qm.ctypes.data_as(_dp),
-                 nf, self._fp.ctypes.data_as(_dp), self._fq.ctypes.data_as(_dp), float(alpha),
-                 float(g_cutoff), float(r_cutoff), int(prec), int(resum_every),
-                 None if self._zm is None else self._zm.ctypes.data_as(_dp),
-                 None if self._zf is None else self._zf.ctypes.data_as(_dp))
         h = _vp()
         if stream is None:
             st = None

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
+from cases import small_case
 from paper_2507_02888_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -60,61 +61,6 @@ def oracle_move(w, walker, pos, k, r_new, rc, gc):
     d_real, d_recip = oracle.delta_e_parts(w["dim"], w["lattice"], p, q, int(k), r_new, w["alpha"], rc, gc)
     de = d_real + d_recip
     return de, max(abs(de), 1e-2 * (abs(d_real) + abs(d_recip)))
-
-
-def small_case(name, W):
-    rng = np.random.default_rng(1234)
-    if name == "sc54":
-        return I.workload("heg3d_sc_n54", W)
-    if name == "fcc100":
-        lat = I.fcc_lattice(100, 1.5)
-        d = dict(dim=3, lattice=lat, n=100, alpha=6.0 / abs(np.linalg.det(lat)) ** (1 / 3))
-        d["pos"] = I.uniform_positions(rng, lat, W, 100)
-        d["q"] = -np.ones(100)
-        d["fixed_pos"], d["fixed_q"] = np.zeros((0, 3)), np.zeros(0)
-    elif name == "hex70":
-        lat = I.hex_lattice(70, 3.0)
-        d = dict(dim=2, lattice=lat, n=70, alpha=5.0 / np.sqrt(abs(np.linalg.det(lat))))
-        d["pos"] = I.uniform_positions(rng, lat, W, 70)
-        d["q"] = -np.ones(70)
-        d["fixed_pos"], d["fixed_q"] = np.zeros((0, 2)), np.zeros(0)
-    elif name == "diamond1":
-        lat, ions = I.diamond_ions(1, 6.74)
-        d = dict(dim=3, lattice=lat, n=32, alpha=0.9)
-        d["pos"] = I.scattered_positions(rng, ions, W, 32, 0.8)
-        d["q"] = -np.ones(32)
-        d["fixed_pos"], d["fixed_q"] = ions, 4.0 * np.ones(len(ions))
-    elif name == "single":
-        lat = I.fcc_lattice(1, 2.0)
-        d = dict(dim=3, lattice=lat, n=1, alpha=2.0)
-        d["pos"] = I.uniform_positions(rng, lat, W, 1)
-        d["q"] = np.array([-1.0])
-        d["fixed_pos"], d["fixed_q"] = np.zeros((0, 3)), np.zeros(0)
-    elif name == "clustered":
-        # half the electrons in a ball of radius 0.25 of the mean spacing:
-        # hundreds of close pairs per 32 x 32 sub-tile, more than the FP32
-        # path's deferred close-pair list holds, so its rescan runs
-        lat = I.sc_lattice(80, 1.5)
-        spacing = abs(np.linalg.det(lat)) ** (1 / 3) / 80 ** (1 / 3)
-        d = dict(dim=3, lattice=lat, n=80, alpha=5.0 / lat[0, 0])
-        pos = I.uniform_positions(rng, lat, W, 80)
-        for k in range(W):
-            v = rng.normal(size=(40, 3))
-            v *= (0.25 * spacing * rng.random((40, 1)) ** (1 / 3)) / np.linalg.norm(v, axis=1, keepdims=True)
-            pos[k, :40] = pos[k, 0] + v
-        d["pos"] = pos
-        d["q"] = -np.ones(80)
-        d["fixed_pos"], d["fixed_q"] = np.zeros((0, 3)), np.zeros(0)
-    elif name == "mixed_q":
-        lat = I.sc_lattice(40, 1.2)
-        d = dict(dim=3, lattice=lat, n=40, alpha=5.0 / lat[0, 0])
-        d["pos"] = I.uniform_positions(rng, lat, W, 40)
-        d["q"] = np.where(np.arange(40) % 4 == 0, 3.0, -1.0)
-        d["fixed_pos"], d["fixed_q"] = np.zeros((0, 3)), np.zeros(0)
-    else:
-        raise KeyError(name)
-    d["n_walkers"] = W
-    return d
 
 
 def make(ew, w, prec, **kw):
@@ -166,6 +112,18 @@ def test_mixed_direct_choice(ew):
         info = ctx.info()
         assert info["mixed_direct"] == flag, name
         assert not flag or 3 <= info["max_candidates"] <= 8
+        ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tiered"])
+def test_plan_reports_what_create_builds(ew, prec, monkeypatch):
+    """ewald_plan (host set-up only) and ewald_get_info of the context
+    ewald_create builds agree field by field (no tiling cache applied)."""
+    monkeypatch.delenv("EWALD_TUNE_CACHE", raising=False)
+    for w in (small_case("fcc100", 1), small_case("hex70", 1), small_case("mixed_q", 1),
+              I.workload("diamond_3x3x3", 1), I.workload("heg3d_fcc_n1024", 1)):
+        ctx = ew.context_for(w, precision=prec)
+        assert ew.plan_for(w, prec) == ctx.info()
         ctx.close()
 
 
