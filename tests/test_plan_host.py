@@ -132,3 +132,21 @@ def test_plan_rejects_bad_descriptions(case, code):
     else:
         got = ewald.load().ewald_plan(None, None)
     assert got == code
+
+
+@pytest.mark.parametrize("name", ["heg3d_fcc_n1024", "heg3d_sc_n54", "diamond_3x3x3", "heg2d_hex_n338"])
+def test_plan_balanced_alpha(name):
+    """gamma <= 0 lets the library pick alpha.  At its choice the real-space
+    work, N particles times the images inside r_c (the r_c sphere's volume, or
+    disc's area, over the cell's), matches the reciprocal work, the number of
+    G vectors inside g_c that the oracle counts, within 5%; and the cutoffs
+    follow the 1e-16 definitions at that alpha."""
+    w = system(name)
+    info = ewald.plan_for(w, "fp64", alpha=0.0)
+    a, dim = info["alpha"], w["dim"]
+    rc, gc = oracle.cutoffs(dim, a)
+    assert abs(info["r_cutoff"] / rc - 1) < 1e-9 and abs(info["g_cutoff"] / gc - 1) < 1e-9
+    n = len(w["q"]) + len(w["fixed_q"])
+    per = (4 * np.pi / 3 * rc ** 3 if dim == 3 else np.pi * rc ** 2) / info["volume"]
+    n_g = oracle.gcount(dim, w["lattice"], gc)
+    assert abs(n * per / n_g - 1) < 0.05, (n * per, n_g)
