@@ -134,7 +134,7 @@ def test_plan_rejects_bad_descriptions(case, code):
     assert got == code
 
 
-@pytest.mark.parametrize("name", ["heg3d_fcc_n1024", "heg3d_sc_n54", "diamond_3x3x3", "heg2d_hex_n338"])
+@pytest.mark.parametrize("name", ["heg3d_fcc_n1024", "sc54", "diamond_3x3x3", "heg2d_hex_n338"])
 def test_plan_balanced_alpha(name):
     """gamma <= 0 lets the library pick alpha.  At its choice the real-space
     work, N particles times the images inside r_c (the r_c sphere's volume, or
