@@ -69,3 +69,13 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    for key in ("metric", "unit", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling", "dtype", "data"):
+        assert key in d, key
+    # the reference arm names the same configuration as the GPU arm: the
+    # workload's sizes and parameters, built by the one function both use
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    from paper_2507_02888_gb300 import inputs
+    args = argparse.Namespace(workload="heg3d_sc_n54", moves=4)
+    assert d["config"] == bench.workload_config(args, inputs.workload("heg3d_sc_n54"), 2)
