@@ -150,3 +150,23 @@ def test_plan_balanced_alpha(name):
     per = (4 * np.pi / 3 * rc ** 3 if dim == 3 else np.pi * rc ** 2) / info["volume"]
     n_g = oracle.gcount(dim, w["lattice"], gc)
     assert abs(n * per / n_g - 1) < 0.05, (n * per, n_g)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["fcc100", "diamond1", "hex70", "sc54", "heg3d_fcc_n1024"])
+def test_plan_image_count(name, prec):
+    """The real-space image list holds every lattice vector R that a wrapped
+    displacement d (fractional coordinates in [-1/2, 1/2)) can bring inside
+    r_c: |R| < r_c + max |d|.  Counted here over a box of integer vectors
+    wide enough for that radius (|m_k| <= reach |b_k| / 2 pi)."""
+    import itertools
+    w = system(name)
+    info = ewald.plan_for(w, prec)
+    A = np.asarray(w["lattice"], dtype=float)
+    dim = A.shape[0]
+    corners = np.array(list(itertools.product([-0.5, 0.5], repeat=dim)))
+    reach = info["r_cutoff"] + np.max(np.linalg.norm(corners @ A, axis=1))
+    B = 2 * np.pi * np.linalg.inv(A).T
+    span = [int(np.ceil(reach * np.linalg.norm(B[k]) / (2 * np.pi))) for k in range(dim)]
+    m = np.array(list(itertools.product(*[range(-s, s + 1) for s in span])), dtype=float)
+    assert info["n_images"] == int(np.sum(np.linalg.norm(m @ A, axis=1) < reach))
